@@ -1,0 +1,175 @@
+/*
+ * bbs.h - batched sparse iterative solvers for GB300 (sm_103a), C ABI.
+ *
+ * Solves many small independent systems A_i x_i = b_i, i = 0..B-1, that share
+ * one sparsity pattern (Sec. 3.1), one CUDA thread block per system (Sec.
+ * 3.2), all systems in one kernel launch (Sec. 3.4). Each system is monitored
+ * and stops on its own residual test (Sec. 2.1); a per-system log records
+ * iterations, final residual and status.
+ *
+ * Conventions for every call:
+ *   - Pointers named in a struct or argument as DEVICE point to device memory
+ *     owned by the caller; the library never frees them. HOST pointers point
+ *     to host memory (pinned memory gives full copy bandwidth).
+ *   - Argument errors are reported before any launch with a bbs_status and a
+ *     message from bbs_last_error(); nothing is written then.
+ *   - Numerical trouble in one system is not an API error: it is recorded in
+ *     that system's log status (bbs_sys_status) and no other system is
+ *     affected.
+ *   - Calls taking a stream are asynchronous on it; the *_host calls return
+ *     after the results are back in host memory.
+ *   - Indices are 0-based int32; columns are sorted ascending within a row.
+ *   - Every device loop is bounded by the iteration caps given in
+ *     bbs_options, so no kernel can run forever.
+ */
+#ifndef BBS_H
+#define BBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BBS_OK = 0,
+    BBS_ERR_INVALID_ARG = 1, /* a size, pointer, enum or option is out of range */
+    BBS_ERR_UNSUPPORTED = 2, /* valid but not provided (e.g. n too large)       */
+    BBS_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has detail) */
+    BBS_ERR_NO_MEMORY = 4    /* workspace too small or a library buffer failed  */
+} bbs_status;
+
+/* Batch matrix formats, Sec. 3.1 and Table "Batched feature support". */
+typedef enum { BBS_FMT_CSR = 0, BBS_FMT_ELL = 1, BBS_FMT_DENSE = 2 } bbs_format;
+/* Solvers, Table "Batched feature support": BatchBicgstab, BatchCg (Alg. 1),
+ * BatchGmres (restarted). */
+typedef enum { BBS_SOLVER_BICGSTAB = 0, BBS_SOLVER_CG = 1, BBS_SOLVER_GMRES = 2 } bbs_solver;
+/* Preconditioners: none, or scalar BatchJacobi M = D^-1 (1 for a zero or
+ * missing diagonal entry). */
+typedef enum { BBS_PREC_NONE = 0, BBS_PREC_JACOBI = 1 } bbs_precond;
+/* Stopping criteria, Table "Batched feature support": stop when
+ * ||b - A x||_2 <= tol (absolute) or <= tol * ||b||_2 (relative). */
+typedef enum { BBS_TOL_ABSOLUTE = 0, BBS_TOL_RELATIVE = 1 } bbs_tol_type;
+/* FP64 throughout, or FP32 inner BiCGSTAB inside FP64 iterative refinement
+ * (residual, update and exit test in FP64). */
+typedef enum { BBS_PRECISION_FP64 = 0, BBS_PRECISION_MIXED_IR = 1 } bbs_precision;
+/* Per-system outcome written to bbs_log.status. */
+typedef enum {
+    BBS_SYS_CONVERGED = 0, /* true residual passed the test                      */
+    BBS_SYS_MAX_ITER = 1,  /* iteration cap reached (or confirmation restarts ran out) */
+    BBS_SYS_BREAKDOWN = 2, /* an exact-zero denominator stopped the method       */
+    BBS_SYS_NAN = 3        /* a non-finite scalar appeared                       */
+} bbs_sys_status;
+
+/* A batch of matrices sharing one pattern (Sec. 3.1). All pointers DEVICE.
+ *   CSR:   row_ptrs [n+1], col_idxs [nnz], values [num_batch * nnz]
+ *   ELL:   col_idxs [ell_k * n] column-major (slot j of row r at j*n + r,
+ *          padding column -1), values [num_batch * ell_k * n] same order,
+ *          padding value 0; row_ptrs unused (may be NULL)
+ *   DENSE: values [num_batch * n * n] row-major; row_ptrs/col_idxs unused
+ * System i's values start at values + i * (nnz | ell_k*n | n*n).
+ * values_f32: optional FP32 copy in the same layout, used by the mixed mode;
+ * NULL makes the library convert into the workspace inside the call. */
+typedef struct {
+    int32_t fmt; /* bbs_format */
+    int32_t num_batch;
+    int32_t n;
+    int32_t nnz;   /* CSR: pattern nonzeros; ELL/DENSE: informational */
+    int32_t ell_k; /* ELL width (max nonzeros per row); ignored otherwise */
+    const int32_t *row_ptrs;
+    const int32_t *col_idxs;
+    const double *values;
+    const float *values_f32;
+} bbs_batch_matrix;
+
+typedef struct {
+    int32_t solver;   /* bbs_solver */
+    int32_t precond;  /* bbs_precond */
+    int32_t tol_type; /* bbs_tol_type */
+    int32_t max_iters;     /* FP64: iteration cap per system (>= 0);
+                              mixed: cap of each inner FP32 solve (>= 1) */
+    double tol;            /* > 0 */
+    int32_t gmres_restart; /* GMRES restart length m, 1..32 */
+    int32_t precision;     /* bbs_precision; mixed requires BiCGSTAB */
+    double inner_tol;      /* mixed: relative tolerance of each inner solve, (0,1) */
+    int32_t max_outer;     /* mixed: cap on refinement steps (>= 0) */
+    int32_t threads_per_system; /* 0: library choice; else a multiple of 32 in
+                                   [32, 1024] with ceil(n / threads) <= 8 */
+    int32_t values_in_smem;     /* 0: library choice, 1: stage each system's
+                                   values in shared memory, -1: read them from
+                                   global memory in every SpMV */
+    int32_t reserved;
+} bbs_options;
+
+/* Per-system log, DEVICE arrays of length num_batch (HOST for *_host calls).
+ *   iters:       iterations taken (FP64 and varsize: Krylov iterations; a
+ *                half-step exit of BiCGSTAB counts as one; GMRES counts
+ *                Arnoldi steps; mixed: refinement steps)
+ *   rel_res:     ||b - A x||_2 / ||b||_2 of the returned x (0 when b = 0)
+ *   status:      bbs_sys_status
+ *   inner_iters: mixed only, total inner FP32 iterations (may be NULL)   */
+typedef struct {
+    int32_t *iters;
+    double *rel_res;
+    int32_t *status;
+    int32_t *inner_iters;
+} bbs_log;
+
+typedef struct bbs_handle bbs_handle;
+
+/* Fill *opts with the defaults: BiCGSTAB, Jacobi, relative tol 1e-10,
+ * max_iters 500, GMRES restart 10, FP64, inner_tol 1e-4, max_outer 30,
+ * library-chosen launch shape. Host only; cannot fail for non-NULL opts. */
+bbs_status bbs_default_options(bbs_options *opts);
+
+/* Create a handle bound to CUDA device `device` (queries its SM count and
+ * shared-memory limit). The handle owns only the buffers of the *_host calls. */
+bbs_status bbs_create(bbs_handle **handle, int device);
+/* Release the handle and the buffers it owns. NULL is accepted. */
+bbs_status bbs_destroy(bbs_handle *handle);
+
+/* Bytes of DEVICE workspace bbs_solve needs for this problem (0 is possible).
+ * Workspace use: the FP32 copy of the values in mixed mode when values_f32
+ * is NULL, and the GMRES Krylov basis when it does not fit in shared memory. */
+bbs_status bbs_workspace_size(const bbs_handle *handle, const bbs_batch_matrix *A,
+                              const bbs_options *opts, size_t *bytes);
+
+/* Solve every system of the batch (Sec. 3.2-3.4: one thread block per system,
+ * one launch for the batch; Sec. 2.1: x holds the initial guess on entry and
+ * the solution on return). b, x: DEVICE [num_batch * n], system i at i*n.
+ * log: DEVICE arrays (see bbs_log). workspace: DEVICE, >= bbs_workspace_size
+ * bytes, 256-byte aligned, may be NULL when that size is 0. stream: a
+ * cudaStream_t (NULL = legacy default stream). Asynchronous. */
+bbs_status bbs_solve(bbs_handle *handle, const bbs_batch_matrix *A, const double *b, double *x,
+                     const bbs_options *opts, const bbs_log *log, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
+/* Same as bbs_solve with every array in HOST memory: A's pointers, b, x (in:
+ * x0, out: x) and log are HOST pointers. The library copies the inputs to
+ * device buffers owned by the handle, solves, copies x and the log back and
+ * waits for completion. */
+bbs_status bbs_solve_host(bbs_handle *handle, const bbs_batch_matrix *A_host,
+                          const double *b_host, double *x_host, const bbs_options *opts,
+                          const bbs_log *log_host);
+
+/* Threads per system by the rule of Sec. 3.6: at least n, a multiple of the
+ * warp size 32, at most `max_threads` (the device maximum, 1024 on GB300).
+ * Returns 0 for n <= 0 or max_threads < 32. Host only. */
+int32_t bbs_paper_block_size(int32_t n, int32_t max_threads);
+
+/* Threads per system the library uses by default for an n-row system: the
+ * fewest warps that keep at most `rows_per_thread` rows per thread (which
+ * keeps the working vectors in registers). Host only. */
+int32_t bbs_default_block_size(int32_t n, int32_t rows_per_thread);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *bbs_last_error(void);
+
+/* Library version string. */
+const char *bbs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BBS_H */

@@ -1,0 +1,248 @@
+"""ctypes binding of libbbs.so (include/bbs.h), argument marshalling only.
+
+Every step of a solve runs in the CUDA library; this module only turns torch
+tensors into the pointers and structs the C ABI takes. If the library has not
+been built, loading raises: there is no fallback of any kind.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libbbs.so")
+
+BBS_OK = 0
+FMT = {"csr": 0, "ell": 1, "dense": 2}
+SOLVER = {"bicgstab": 0, "cg": 1, "gmres": 2}
+PRECOND = {"none": 0, "jacobi": 1}
+TOL = {"absolute": 0, "relative": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+SYS_STATUS = {0: "converged", 1: "max_iter", 2: "breakdown", 3: "nan"}
+
+
+class bbs_batch_matrix(C.Structure):
+    _fields_ = [("fmt", C.c_int32), ("num_batch", C.c_int32), ("n", C.c_int32),
+                ("nnz", C.c_int32), ("ell_k", C.c_int32), ("row_ptrs", C.c_void_p),
+                ("col_idxs", C.c_void_p), ("values", C.c_void_p), ("values_f32", C.c_void_p)]
+
+
+class bbs_options(C.Structure):
+    _fields_ = [("solver", C.c_int32), ("precond", C.c_int32), ("tol_type", C.c_int32),
+                ("max_iters", C.c_int32), ("tol", C.c_double), ("gmres_restart", C.c_int32),
+                ("precision", C.c_int32), ("inner_tol", C.c_double), ("max_outer", C.c_int32),
+                ("threads_per_system", C.c_int32), ("values_in_smem", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class bbs_log(C.Structure):
+    _fields_ = [("iters", C.c_void_p), ("rel_res", C.c_void_p), ("status", C.c_void_p),
+                ("inner_iters", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libbbs.so; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        L.bbs_default_options.argtypes = [P(bbs_options)]
+        L.bbs_create.argtypes = [P(C.c_void_p), C.c_int]
+        L.bbs_destroy.argtypes = [C.c_void_p]
+        L.bbs_workspace_size.argtypes = [C.c_void_p, P(bbs_batch_matrix), P(bbs_options),
+                                         P(C.c_size_t)]
+        L.bbs_solve.argtypes = [C.c_void_p, P(bbs_batch_matrix), C.c_void_p, C.c_void_p,
+                                P(bbs_options), P(bbs_log), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.bbs_solve_host.argtypes = [C.c_void_p, P(bbs_batch_matrix), C.c_void_p, C.c_void_p,
+                                     P(bbs_options), P(bbs_log)]
+        L.bbs_paper_block_size.argtypes = [C.c_int32, C.c_int32]
+        L.bbs_paper_block_size.restype = C.c_int32
+        L.bbs_default_block_size.argtypes = [C.c_int32, C.c_int32]
+        L.bbs_default_block_size.restype = C.c_int32
+        L.bbs_last_error.restype = C.c_char_p
+        L.bbs_version.restype = C.c_char_p
+        for name in ("bbs_default_options", "bbs_create", "bbs_destroy", "bbs_workspace_size",
+                     "bbs_solve", "bbs_solve_host"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class BBSError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().bbs_last_error().decode()
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != BBS_OK:
+        raise BBSError(status, where)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def bbs_default_options(**overrides) -> bbs_options:
+    o = bbs_options()
+    _check(lib().bbs_default_options(C.byref(o)), "bbs_default_options")
+    for k, v in overrides.items():
+        if k == "solver":
+            v = SOLVER[v] if isinstance(v, str) else v
+        elif k == "precond":
+            v = PRECOND[v] if isinstance(v, str) else v
+        elif k == "tol_type":
+            v = TOL[v] if isinstance(v, str) else v
+        elif k == "precision":
+            v = PRECISION[v] if isinstance(v, str) else v
+        setattr(o, k, v)
+    return o
+
+
+def bbs_paper_block_size(n: int, max_threads: int = 1024) -> int:
+    return int(lib().bbs_paper_block_size(n, max_threads))
+
+
+def bbs_default_block_size(n: int, rows_per_thread: int = 5) -> int:
+    return int(lib().bbs_default_block_size(n, rows_per_thread))
+
+
+def bbs_version() -> str:
+    return lib().bbs_version().decode()
+
+
+@dataclass
+class DeviceBatch:
+    """Tensors of one batch matrix (Sec. 3.1 layouts), on one device or on the host."""
+
+    fmt: str
+    n: int
+    nnz: int
+    ell_k: int
+    row_ptrs: torch.Tensor | None
+    col_idxs: torch.Tensor | None
+    values: torch.Tensor
+    values_f32: torch.Tensor | None = None
+
+    @property
+    def num_batch(self) -> int:
+        return int(self.values.shape[0])
+
+    @classmethod
+    def from_batch(cls, A, device="cuda", values_f32: bool = False, pin: bool = False):
+        """From a workloads.BatchMatrix (numpy) to tensors on `device`."""
+        def t(a, dtype):
+            if a is None:
+                return None
+            x = torch.as_tensor(a).to(dtype)
+            if device == "cpu":
+                return x.pin_memory() if pin else x.contiguous()
+            return x.to(device)
+        vals = t(A.values, torch.float64)
+        rp = t(A.row_ptrs, torch.int32) if A.fmt == "csr" else None
+        ci = t(A.col_idxs, torch.int32) if A.fmt in ("csr", "ell") else None
+        v32 = vals.to(torch.float32) if values_f32 else None
+        return cls(A.fmt, A.n, A.nnz, A.ell_k, rp, ci, vals, v32)
+
+    def struct(self) -> bbs_batch_matrix:
+        return bbs_batch_matrix(FMT[self.fmt], self.num_batch, self.n, self.nnz, self.ell_k,
+                                _ptr(self.row_ptrs), _ptr(self.col_idxs), _ptr(self.values),
+                                _ptr(self.values_f32))
+
+
+@dataclass
+class Log:
+    iters: torch.Tensor
+    rel_res: torch.Tensor
+    status: torch.Tensor
+    inner_iters: torch.Tensor | None = None
+
+    @classmethod
+    def empty(cls, num_batch: int, device="cuda", inner: bool = False, pin: bool = False):
+        kw = dict(device=device)
+        mk = (lambda *a, **k: torch.empty(*a, **k).pin_memory()) if pin else torch.empty
+        return cls(mk(num_batch, dtype=torch.int32, **kw), mk(num_batch, dtype=torch.float64, **kw),
+                   mk(num_batch, dtype=torch.int32, **kw),
+                   mk(num_batch, dtype=torch.int32, **kw) if inner else None)
+
+    def struct(self) -> bbs_log:
+        return bbs_log(_ptr(self.iters), _ptr(self.rel_res), _ptr(self.status), _ptr(self.inner_iters))
+
+
+class Handle:
+    """Owns a bbs_handle for one device."""
+
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().bbs_create(C.byref(h), int(device)), "bbs_create")
+        self._h = h
+        self.device = int(device)
+
+    def close(self):
+        if self._h:
+            lib().bbs_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_size(self, A: DeviceBatch, opts: bbs_options) -> int:
+        out = C.c_size_t()
+        s = A.struct()
+        _check(lib().bbs_workspace_size(self._h, C.byref(s), C.byref(opts), C.byref(out)),
+               "bbs_workspace_size")
+        return int(out.value)
+
+    def workspace(self, A: DeviceBatch, opts: bbs_options) -> torch.Tensor | None:
+        nb = self.workspace_size(A, opts)
+        if nb == 0:
+            return None
+        return torch.empty(nb, dtype=torch.uint8, device=A.values.device)
+
+    def solve(self, A: DeviceBatch, b: torch.Tensor, x: torch.Tensor, opts: bbs_options,
+              log: Log, workspace: torch.Tensor | None = None, stream=None):
+        """bbs_solve: x (in: x0, out: solution) and log are written asynchronously."""
+        s = A.struct()
+        lg = log.struct()
+        ws_bytes = 0 if workspace is None else workspace.numel() * workspace.element_size()
+        st = stream if stream is not None else torch.cuda.current_stream(A.values.device)
+        _check(lib().bbs_solve(self._h, C.byref(s), _ptr(b), _ptr(x), C.byref(opts), C.byref(lg),
+                               _ptr(workspace), ws_bytes, C.c_void_p(st.cuda_stream)), "bbs_solve")
+
+    def solve_host(self, A: DeviceBatch, b: torch.Tensor, x: torch.Tensor, opts: bbs_options,
+                   log: Log):
+        """bbs_solve_host: every tensor in host memory; returns when results are back."""
+        s = A.struct()
+        lg = log.struct()
+        _check(lib().bbs_solve_host(self._h, C.byref(s), _ptr(b), _ptr(x), C.byref(opts),
+                                    C.byref(lg)), "bbs_solve_host")
+
+
+def solve(A: DeviceBatch, b: torch.Tensor, x0: torch.Tensor | None = None, handle: Handle | None = None,
+          **opts):
+    """Convenience: allocate x, log and workspace, solve on the current stream.
+
+    Returns (x, Log). opts are bbs_options fields (strings allowed for enums).
+    """
+    dev = A.values.device
+    h = handle or Handle(dev.index or 0)
+    o = bbs_default_options(**opts)
+    x = (torch.zeros_like(b) if x0 is None else x0.clone()).contiguous()
+    log = Log.empty(A.num_batch, device=dev, inner=(o.precision == 1))
+    ws = h.workspace(A, o)
+    h.solve(A, b.contiguous(), x, o, log, ws)
+    return x, log

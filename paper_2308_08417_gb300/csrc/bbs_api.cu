@@ -1,0 +1,400 @@
+// Host side of the C ABI declared in include/bbs.h: argument checks, the
+// launch-shape choice, the kernel dispatch over (solver, format, precision,
+// rows per thread) (Sec. 3.3's multi-level dispatch) and the host-buffer path.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bbs.h"
+#include "bbs_kernels.h"
+#include "bbs_params.h"
+
+struct bbs_handle {
+    int device = 0;
+    int sms = 0;
+    int max_smem_optin = 0;
+    int max_threads = 1024;
+    cudaStream_t stream = nullptr;  // used by bbs_solve_host
+    // device buffers owned for bbs_solve_host (grow only)
+    void* buf[12] = {nullptr};
+    size_t cap[12] = {0};
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bbs_status fail(bbs_status s, const char* fmt, ...) {
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    g_last_error = msg;
+    return s;
+}
+
+bbs_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(BBS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t vals_per_system(const bbs_batch_matrix* A) {
+    switch (A->fmt) {
+        case BBS_FMT_CSR: return (size_t)A->nnz;
+        case BBS_FMT_ELL: return (size_t)A->ell_k * (size_t)A->n;
+        default: return (size_t)A->n * (size_t)A->n;
+    }
+}
+
+constexpr int kDefaultRowsPerThread = 5;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Launch plan for one solve.
+struct Plan {
+    int threads = 0, R = 0, n_pad = 0;
+    size_t smem = 0;        // dynamic shared memory bytes
+    size_t stage_off = 0;
+    bool stage = false;
+    bool gmres_ws = false;  // GMRES basis in the workspace
+    size_t ws_gmres = 0, ws_f32 = 0;
+};
+
+bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
+    if (A == nullptr || o == nullptr) return fail(BBS_ERR_INVALID_ARG, "null matrix or options");
+    if (A->fmt < 0 || A->fmt > 2) return fail(BBS_ERR_INVALID_ARG, "unknown format %d", A->fmt);
+    if (A->num_batch < 0) return fail(BBS_ERR_INVALID_ARG, "num_batch < 0");
+    if (A->n <= 0) return fail(BBS_ERR_INVALID_ARG, "n must be positive (got %d)", A->n);
+    if (A->fmt == BBS_FMT_CSR && (A->nnz < 0 || A->row_ptrs == nullptr || A->col_idxs == nullptr))
+        return fail(BBS_ERR_INVALID_ARG, "CSR needs nnz >= 0, row_ptrs and col_idxs");
+    if (A->fmt == BBS_FMT_ELL) {
+        if (A->ell_k <= 0 || A->col_idxs == nullptr)
+            return fail(BBS_ERR_INVALID_ARG, "ELL needs ell_k > 0 and col_idxs");
+        if ((long long)A->ell_k * A->n > 0x7fffffffLL)
+            return fail(BBS_ERR_INVALID_ARG, "ELL ell_k*n overflows int32");
+    }
+    if (A->fmt == BBS_FMT_DENSE && (long long)A->n * A->n > 0x7fffffffLL)
+        return fail(BBS_ERR_INVALID_ARG, "dense n*n overflows int32");
+    if (A->num_batch > 0 && A->values == nullptr) return fail(BBS_ERR_INVALID_ARG, "values is NULL");
+    if (o->solver < 0 || o->solver > 2) return fail(BBS_ERR_INVALID_ARG, "unknown solver %d", o->solver);
+    if (o->precond < 0 || o->precond > 1) return fail(BBS_ERR_INVALID_ARG, "unknown preconditioner %d", o->precond);
+    if (o->tol_type < 0 || o->tol_type > 1) return fail(BBS_ERR_INVALID_ARG, "unknown tolerance type %d", o->tol_type);
+    if (!(o->tol > 0.0)) return fail(BBS_ERR_INVALID_ARG, "tol must be > 0");
+    if (o->max_iters < 0) return fail(BBS_ERR_INVALID_ARG, "max_iters must be >= 0");
+    if (o->precision < 0 || o->precision > 1) return fail(BBS_ERR_INVALID_ARG, "unknown precision %d", o->precision);
+    if (o->solver == BBS_SOLVER_GMRES && (o->gmres_restart < 1 || o->gmres_restart > 32))
+        return fail(BBS_ERR_INVALID_ARG, "gmres_restart must be in [1, 32]");
+    if (o->precision == BBS_PRECISION_MIXED_IR) {
+        if (o->solver != BBS_SOLVER_BICGSTAB)
+            return fail(BBS_ERR_UNSUPPORTED, "mixed precision is provided for BiCGSTAB only");
+        if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0))
+            return fail(BBS_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+        if (o->max_outer < 0 || o->max_iters < 1)
+            return fail(BBS_ERR_INVALID_ARG, "mixed mode needs max_outer >= 0 and max_iters >= 1");
+    }
+    const int t = o->threads_per_system;
+    if (t != 0 && (t < 32 || t > 1024 || (t % 32) != 0))
+        return fail(BBS_ERR_INVALID_ARG, "threads_per_system must be 0 or a multiple of 32 in [32, 1024]");
+    if (o->values_in_smem < -1 || o->values_in_smem > 1)
+        return fail(BBS_ERR_INVALID_ARG, "values_in_smem must be -1, 0 or 1");
+    return BBS_OK;
+}
+
+int max_row_len(const bbs_batch_matrix* A) { return A->fmt == BBS_FMT_ELL ? A->ell_k : 0; }
+
+bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_options* o, Plan* p) {
+    const int n = A->n;
+    p->threads = o->threads_per_system ? o->threads_per_system
+                                       : bbs_default_block_size(n, kDefaultRowsPerThread);
+    if (p->threads <= 0)
+        return fail(BBS_ERR_UNSUPPORTED, "n = %d exceeds the largest supported system (%d rows)", n,
+                    bbs::kMaxRows);
+    p->R = (n + p->threads - 1) / p->threads;
+    if (p->R > bbs::kMaxR || p->threads > bbs::max_threads_for(p->R))
+        return fail(BBS_ERR_INVALID_ARG,
+                    "threads_per_system %d leaves %d rows per thread; R = 1 allows 1024 threads, "
+                    "R <= 4 512, R <= 8 256", p->threads, p->R);
+    p->n_pad = (n + 1) & ~1;
+    const bool mixed = o->precision == BBS_PRECISION_MIXED_IR;
+    const size_t vps = vals_per_system(A);
+    size_t base;
+    if (mixed) {
+        base = 256 * 8 + (size_t)p->n_pad * 8 + 256 * 4 + 2 * (size_t)p->n_pad * 4;
+    } else {
+        base = 256 * 8 + 2 * (size_t)p->n_pad * 8;
+        if (o->solver == BBS_SOLVER_GMRES) {
+            const size_t m = (size_t)o->gmres_restart;
+            base += ((m + 1) * m + 2 * m + (m + 1) + m + 2) * 8;
+            const size_t vbytes = (m + 1) * (size_t)p->n_pad * 8;
+            if (base + vbytes <= (size_t)h->max_smem_optin) {
+                base += vbytes;
+            } else {
+                p->gmres_ws = true;
+                p->ws_gmres = vbytes * (size_t)A->num_batch;
+            }
+        }
+    }
+    base = align_up(base, 16);
+    const size_t stage_bytes = align_up(vps * (mixed ? 4 : 8), 16);
+    const size_t limit = (size_t)h->max_smem_optin;
+    bool stage = false;
+    if (o->values_in_smem == 1)
+        stage = base + stage_bytes <= limit;
+    else if (o->values_in_smem == 0)
+        stage = base + stage_bytes <= 64 * 1024;
+    if (base > limit) return fail(BBS_ERR_UNSUPPORTED, "shared memory need %zu exceeds %zu", base, limit);
+    p->stage = stage;
+    p->stage_off = base;
+    p->smem = base + (stage ? stage_bytes : 0);
+    if (mixed && A->values_f32 == nullptr) p->ws_f32 = align_up(vps * 4 * (size_t)A->num_batch, 256);
+    return BBS_OK;
+}
+
+size_t workspace_bytes(const Plan& p) { return align_up(p.ws_gmres, 256) + p.ws_f32; }
+
+const void* pick_kernel(const bbs_options* o, int fmt, int R) {
+    if (o->precision == BBS_PRECISION_MIXED_IR) return bbs::refine_fn(fmt, R);
+    switch (o->solver) {
+        case BBS_SOLVER_CG: return bbs::cg_fn(fmt, R);
+        case BBS_SOLVER_GMRES: return bbs::gmres_fn(fmt, R);
+        default: return bbs::bicgstab_fn(fmt, R);
+    }
+}
+
+std::mutex g_attr_mutex;
+
+cudaError_t allow_smem(const void* fn, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+extern "C" {
+
+bbs_status bbs_default_options(bbs_options* o) {
+    if (o == nullptr) return fail(BBS_ERR_INVALID_ARG, "null options");
+    std::memset(o, 0, sizeof *o);
+    o->solver = BBS_SOLVER_BICGSTAB;
+    o->precond = BBS_PREC_JACOBI;
+    o->tol_type = BBS_TOL_RELATIVE;
+    o->tol = 1e-10;
+    o->max_iters = 500;
+    o->gmres_restart = 10;
+    o->precision = BBS_PRECISION_FP64;
+    o->inner_tol = 1e-4;
+    o->max_outer = 30;
+    return BBS_OK;
+}
+
+int32_t bbs_paper_block_size(int32_t n, int32_t max_threads) {
+    if (n <= 0 || max_threads < 32) return 0;
+    const int32_t cap = max_threads / 32 * 32;
+    const int32_t up = (n + 31) / 32 * 32;
+    return up < cap ? up : cap;
+}
+
+int32_t bbs_default_block_size(int32_t n, int32_t rows_per_thread) {
+    if (n <= 0 || rows_per_thread <= 0 || n > bbs::kMaxRows) return 0;
+    const int32_t rpt = rows_per_thread < bbs::kMaxR ? rows_per_thread : bbs::kMaxR;
+    for (int32_t r = rpt; r >= 1; --r) {  // fewest warps at <= r rows per thread
+        const int32_t threads = (n + 32 * r - 1) / (32 * r) * 32;
+        if (threads > 1024) continue;
+        const int32_t R = (n + threads - 1) / threads;
+        if (threads <= bbs::max_threads_for(R)) return threads;
+    }
+    return 0;
+}
+
+const char* bbs_last_error(void) { return g_last_error.c_str(); }
+
+const char* bbs_version(void) { return "bbs 0.1 sm_103a"; }
+
+bbs_status bbs_create(bbs_handle** handle, int device) {
+    if (handle == nullptr) return fail(BBS_ERR_INVALID_ARG, "null handle pointer");
+    *handle = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return fail(BBS_ERR_INVALID_ARG, "device %d out of range", device);
+    bbs_handle* h = new bbs_handle();
+    h->device = device;
+    if ((e = cudaSetDevice(device)) != cudaSuccess) { delete h; return cuda_fail(e, "cudaSetDevice"); }
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&h->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaDeviceGetAttribute(&h->max_threads, cudaDevAttrMaxThreadsPerBlock, device);
+    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    *handle = h;
+    return BBS_OK;
+}
+
+bbs_status bbs_destroy(bbs_handle* h) {
+    if (h == nullptr) return BBS_OK;
+    cudaSetDevice(h->device);
+    for (int i = 0; i < 12; ++i)
+        if (h->buf[i]) cudaFree(h->buf[i]);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return BBS_OK;
+}
+
+bbs_status bbs_workspace_size(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_options* o,
+                              size_t* bytes) {
+    if (h == nullptr || bytes == nullptr) return fail(BBS_ERR_INVALID_ARG, "null handle or output");
+    bbs_status s = validate(A, o);
+    if (s != BBS_OK) return s;
+    Plan p;
+    if ((s = make_plan(h, A, o, &p)) != BBS_OK) return s;
+    *bytes = workspace_bytes(p);
+    return BBS_OK;
+}
+
+bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, double* x,
+                     const bbs_options* o, const bbs_log* log, void* workspace,
+                     size_t ws_bytes, void* stream) {
+    if (h == nullptr) return fail(BBS_ERR_INVALID_ARG, "null handle");
+    bbs_status s = validate(A, o);
+    if (s != BBS_OK) return s;
+    if (log == nullptr || log->iters == nullptr || log->rel_res == nullptr || log->status == nullptr)
+        return fail(BBS_ERR_INVALID_ARG, "log arrays iters, rel_res and status are required");
+    if (A->num_batch > 0 && (b == nullptr || x == nullptr))
+        return fail(BBS_ERR_INVALID_ARG, "b and x are required");
+    Plan p;
+    if ((s = make_plan(h, A, o, &p)) != BBS_OK) return s;
+    const size_t need = workspace_bytes(p);
+    if (ws_bytes < need || (need > 0 && workspace == nullptr))
+        return fail(BBS_ERR_NO_MEMORY, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    if (need > 0 && (reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+        return fail(BBS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (A->num_batch == 0) return BBS_OK;
+    cudaSetDevice(h->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    bbs::SolveParams P{};
+    P.n = A->n;
+    P.n_pad = p.n_pad;
+    P.k = max_row_len(A);
+    P.num_batch = A->num_batch;
+    P.vps = vals_per_system(A);
+    P.row_ptrs = A->row_ptrs;
+    P.cols = A->col_idxs;
+    P.values = A->values;
+    P.values32 = A->values_f32;
+    P.b = b;
+    P.x = x;
+    P.iters = log->iters;
+    P.rel_res = log->rel_res;
+    P.status = log->status;
+    P.inner_iters = log->inner_iters;
+    P.precond = o->precond;
+    P.tol_type = o->tol_type;
+    P.tol = o->tol;
+    P.max_iters = o->max_iters;
+    P.restart = o->gmres_restart;
+    P.inner_tol = o->inner_tol;
+    P.max_outer = o->max_outer;
+    P.stage = p.stage ? 1 : 0;
+    P.stage_off = p.stage_off;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    P.ws = p.gmres_ws ? reinterpret_cast<double*>(ws) : nullptr;
+    cudaError_t e;
+    if (p.ws_f32 > 0) {
+        float* f32 = reinterpret_cast<float*>(ws + align_up(p.ws_gmres, 256));
+        if ((e = bbs::launch_convert_f32(A->values, f32, P.vps * (size_t)A->num_batch, st)) != cudaSuccess)
+            return cuda_fail(e, "FP32 conversion launch");
+        P.values32 = f32;
+    }
+    const void* fn = pick_kernel(o, A->fmt, p.R);
+    if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    void* args[] = {&P};
+    e = cudaLaunchKernel(fn, dim3((unsigned)A->num_batch), dim3((unsigned)p.threads), args, p.smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+    return BBS_OK;
+}
+
+static bbs_status ensure(bbs_handle* h, int slot, size_t bytes, void** out) {
+    if (bytes == 0) {
+        *out = nullptr;
+        return BBS_OK;
+    }
+    if (h->cap[slot] < bytes) {
+        if (h->buf[slot]) cudaFree(h->buf[slot]);
+        h->buf[slot] = nullptr;
+        h->cap[slot] = 0;
+        cudaError_t e = cudaMalloc(&h->buf[slot], bytes);
+        if (e != cudaSuccess) return fail(BBS_ERR_NO_MEMORY, "device buffer of %zu bytes: %s", bytes, cudaGetErrorString(e));
+        h->cap[slot] = bytes;
+    }
+    *out = h->buf[slot];
+    return BBS_OK;
+}
+
+bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const double* b_host,
+                          double* x_host, const bbs_options* o, const bbs_log* log_host) {
+    if (h == nullptr) return fail(BBS_ERR_INVALID_ARG, "null handle");
+    bbs_status s = validate(Ah, o);
+    if (s != BBS_OK) return s;
+    if (log_host == nullptr || log_host->iters == nullptr || log_host->rel_res == nullptr ||
+        log_host->status == nullptr)
+        return fail(BBS_ERR_INVALID_ARG, "log arrays iters, rel_res and status are required");
+    const size_t B = (size_t)Ah->num_batch, n = (size_t)Ah->n;
+    if (B == 0) return BBS_OK;
+    if (b_host == nullptr || x_host == nullptr) return fail(BBS_ERR_INVALID_ARG, "b and x are required");
+    cudaSetDevice(h->device);
+    const size_t vps = vals_per_system(Ah);
+    const size_t rp_bytes = Ah->fmt == BBS_FMT_CSR ? (n + 1) * 4 : 0;
+    const size_t ci_bytes = Ah->fmt == BBS_FMT_CSR ? (size_t)Ah->nnz * 4
+                            : Ah->fmt == BBS_FMT_ELL ? (size_t)Ah->ell_k * n * 4 : 0;
+    void *d_rp, *d_ci, *d_v, *d_v32, *d_b, *d_x, *d_it, *d_rr, *d_st, *d_in, *d_ws;
+    if ((s = ensure(h, 0, rp_bytes, &d_rp)) || (s = ensure(h, 1, ci_bytes, &d_ci)) ||
+        (s = ensure(h, 2, B * vps * 8, &d_v)) ||
+        (s = ensure(h, 3, Ah->values_f32 ? B * vps * 4 : 0, &d_v32)) ||
+        (s = ensure(h, 4, B * n * 8, &d_b)) || (s = ensure(h, 5, B * n * 8, &d_x)) ||
+        (s = ensure(h, 6, B * 4, &d_it)) || (s = ensure(h, 7, B * 8, &d_rr)) ||
+        (s = ensure(h, 8, B * 4, &d_st)) ||
+        (s = ensure(h, 9, log_host->inner_iters ? B * 4 : 0, &d_in)))
+        return s;
+    bbs_batch_matrix Ad = *Ah;
+    Ad.row_ptrs = static_cast<const int32_t*>(d_rp);
+    Ad.col_idxs = static_cast<const int32_t*>(d_ci);
+    Ad.values = static_cast<const double*>(d_v);
+    Ad.values_f32 = static_cast<const float*>(d_v32);
+    size_t ws_bytes = 0;
+    if ((s = bbs_workspace_size(h, &Ad, o, &ws_bytes)) != BBS_OK) return s;
+    if ((s = ensure(h, 10, ws_bytes, &d_ws)) != BBS_OK) return s;
+    cudaStream_t st = h->stream;
+    cudaError_t e = cudaSuccess;
+#define BBS_CP(dst, src, bytes, kind)                                              \
+    if ((bytes) > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, kind, st)
+    BBS_CP(d_rp, Ah->row_ptrs, rp_bytes, cudaMemcpyHostToDevice);
+    BBS_CP(d_ci, Ah->col_idxs, ci_bytes, cudaMemcpyHostToDevice);
+    BBS_CP(d_v, Ah->values, B * vps * 8, cudaMemcpyHostToDevice);
+    if (Ah->values_f32) BBS_CP(d_v32, Ah->values_f32, B * vps * 4, cudaMemcpyHostToDevice);
+    BBS_CP(d_b, b_host, B * n * 8, cudaMemcpyHostToDevice);
+    BBS_CP(d_x, x_host, B * n * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    bbs_log dlog{static_cast<int32_t*>(d_it), static_cast<double*>(d_rr), static_cast<int32_t*>(d_st),
+                 static_cast<int32_t*>(d_in)};
+    if ((s = bbs_solve(h, &Ad, static_cast<const double*>(d_b), static_cast<double*>(d_x), o, &dlog,
+                       d_ws, ws_bytes, st)) != BBS_OK)
+        return s;
+    BBS_CP(x_host, d_x, B * n * 8, cudaMemcpyDeviceToHost);
+    BBS_CP(log_host->iters, d_it, B * 4, cudaMemcpyDeviceToHost);
+    BBS_CP(log_host->rel_res, d_rr, B * 8, cudaMemcpyDeviceToHost);
+    BBS_CP(log_host->status, d_st, B * 4, cudaMemcpyDeviceToHost);
+    if (log_host->inner_iters) BBS_CP(log_host->inner_iters, d_in, B * 4, cudaMemcpyDeviceToHost);
+#undef BBS_CP
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "solve");
+    return BBS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,271 @@
+// Device building blocks of the fused batched solvers (Sec. 3.2): SpMV per
+// batch format, block-wide dot products and norms, Jacobi setup.
+//
+// Thread mapping. One thread block owns one system. Thread `tid` of a block
+// of `nt` threads owns rows tid, tid + nt, ..., tid + (R-1)*nt (R is a
+// compile-time bound, ceil(n / nt) <= R). Every vector the method updates
+// element-wise (r, r^, p, v, x, dinv ...) lives in the owner's registers;
+// only the SpMV input vectors, which every thread reads at arbitrary columns,
+// go through shared memory. This is the GB300 counterpart of the paper's
+// "vectors in SLM by priority" (Sec. 3.5): registers are the faster and
+// larger store here, so the priority list collapses to "SpMV inputs in shared
+// memory, everything else in registers".
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bbs_kernels.h"
+
+namespace bbs {
+
+enum Fmt { FMT_CSR = 0, FMT_ELL = 1, FMT_DENSE = 2 };
+enum SysStatus { ST_CONVERGED = 0, ST_MAX_ITER = 1, ST_BREAKDOWN = 2, ST_NAN = 3 };
+constexpr int kMaxRestarts = 3;  // confirmation restarts before MAX_ITER
+constexpr unsigned kFull = 0xffffffffu;
+
+// One system's matrix. vals points at this system's first value.
+template <typename V>
+struct Mat {
+    const V* __restrict__ vals;
+    const int32_t* __restrict__ row_ptrs;  // CSR
+    const int32_t* __restrict__ cols;      // CSR: nnz, ELL: k*n column-major
+    int n;
+    int k;  // ELL width
+};
+
+struct Team {
+    int tid, nt, lane, warp, nwarps;
+    __device__ __forceinline__ static Team make() {
+        Team t;
+        t.tid = threadIdx.x;
+        t.nt = blockDim.x;
+        t.lane = threadIdx.x & 31;
+        t.warp = threadIdx.x >> 5;
+        t.nwarps = blockDim.x >> 5;
+        return t;
+    }
+    __device__ __forceinline__ int row(int q) const { return tid + q * nt; }
+    __device__ __forceinline__ void sync() const {
+        if (nwarps == 1)
+            __syncwarp();
+        else
+            __syncthreads();
+    }
+};
+
+template <typename V>
+__device__ __forceinline__ V ldg(const V* p) { return __ldg(p); }
+
+template <typename T>
+__device__ __forceinline__ bool finite(T v) { return isfinite(v); }
+
+// a_ii of row `row` (0 when the pattern stores none).
+template <int FMT, typename V>
+__device__ __forceinline__ V diag_entry(const Mat<V>& A, int row) {
+    if constexpr (FMT == FMT_CSR) {
+        const int e0 = ldg(A.row_ptrs + row), e1 = ldg(A.row_ptrs + row + 1);
+        for (int e = e0; e < e1; ++e)
+            if (ldg(A.cols + e) == row) return ldg(A.vals + e);
+        return V(0);
+    } else if constexpr (FMT == FMT_ELL) {
+        for (int j = 0; j < A.k; ++j)
+            if (ldg(A.cols + (size_t)j * A.n + row) == row) return ldg(A.vals + (size_t)j * A.n + row);
+        return V(0);
+    } else {
+        return ldg(A.vals + (size_t)row * A.n + row);
+    }
+}
+
+// Scalar Jacobi (Table "Batched feature support": BatchJacobi): 1/a_ii, with
+// 1 for a zero or missing diagonal; without preconditioning all ones. Rows
+// beyond n get 0 so that they stay inert in every update and dot product.
+template <int FMT, int R, typename T, typename V>
+__device__ __forceinline__ void jacobi_setup(const Mat<V>& A, bool jacobi, T (&dinv)[R],
+                                             const Team& tm) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        T d = T(0);
+        if (row < A.n) {
+            const T a = jacobi ? T(diag_entry<FMT>(A, row)) : T(0);
+            d = (a != T(0)) ? T(1) / a : T(1);
+        }
+        dinv[q] = d;
+    }
+}
+
+// y = A x for the caller's rows; x is a shared-memory vector of length n.
+// Entries are accumulated in stored (ascending column) order with FMA.
+template <int FMT, int R, typename T, typename V>
+__device__ __forceinline__ void spmv(const Mat<V>& A, const T* __restrict__ xs, T (&y)[R],
+                                     const Team& tm) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        T sum = T(0);
+        if (row < A.n) {
+            if constexpr (FMT == FMT_ELL) {
+                const int32_t* c = A.cols + row;
+                const V* a = A.vals + row;
+                for (int j = 0; j < A.k; ++j) {
+                    const int col = ldg(c + (size_t)j * A.n);
+                    if (col >= 0) sum = fma(T(ldg(a + (size_t)j * A.n)), xs[col], sum);
+                }
+            } else if constexpr (FMT == FMT_CSR) {
+                const int e0 = ldg(A.row_ptrs + row), e1 = ldg(A.row_ptrs + row + 1);
+                for (int e = e0; e < e1; ++e) sum = fma(T(ldg(A.vals + e)), xs[ldg(A.cols + e)], sum);
+            } else {
+                const V* a = A.vals + (size_t)row * A.n;
+                for (int j = 0; j < A.n; ++j) sum = fma(T(ldg(a + j)), xs[j], sum);
+            }
+        }
+        y[q] = sum;
+    }
+}
+
+// Same SpMV with the system's values staged in shared memory (as, laid out
+// exactly like the global values of the system).
+template <int FMT, int R, typename T, typename V>
+__device__ __forceinline__ void spmv_staged(const Mat<V>& A, const V* __restrict__ as,
+                                            const T* __restrict__ xs, T (&y)[R], const Team& tm) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        T sum = T(0);
+        if (row < A.n) {
+            if constexpr (FMT == FMT_ELL) {
+                for (int j = 0; j < A.k; ++j) {
+                    const int col = ldg(A.cols + (size_t)j * A.n + row);
+                    if (col >= 0) sum = fma(T(as[(size_t)j * A.n + row]), xs[col], sum);
+                }
+            } else if constexpr (FMT == FMT_CSR) {
+                const int e0 = ldg(A.row_ptrs + row), e1 = ldg(A.row_ptrs + row + 1);
+                for (int e = e0; e < e1; ++e) sum = fma(T(as[e]), xs[ldg(A.cols + e)], sum);
+            } else {
+                const V* a = as + (size_t)row * A.n;
+                for (int j = 0; j < A.n; ++j) sum = fma(T(a[j]), xs[j], sum);
+            }
+        }
+        y[q] = sum;
+    }
+}
+
+// Copy `count` values from global to shared memory with the whole block
+// (16-byte vector loads when both ends allow it).
+template <typename V>
+__device__ __forceinline__ void stage_values(const V* __restrict__ g, V* __restrict__ s,
+                                             size_t count, const Team& tm) {
+    constexpr int kVec = 16 / sizeof(V);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(g) & 15) == 0);
+    size_t i = 0;
+    if (aligned) {
+        const size_t nv = count / kVec;
+        const uint4* gv = reinterpret_cast<const uint4*>(g);
+        uint4* sv = reinterpret_cast<uint4*>(s);
+        for (size_t j = tm.tid; j < nv; j += tm.nt) sv[j] = __ldg(gv + j);
+        i = nv * kVec;
+    }
+    for (size_t j = i + tm.tid; j < count; j += tm.nt) s[j] = ldg(g + j);
+}
+
+// ------------------------------------------------------------ reductions
+//
+// Block-wide sums of NV values at once, returned to every thread with
+// identical bits. Within a warp the NV values are reduced "transposed": the
+// first butterfly levels exchange half of the values instead of all, so NV
+// sums cost about NV-1+5 additions instead of 5*NV (FP64 additions are the
+// scarce resource on GB300). IEEE addition is commutative, so butterfly
+// partners always hold identical sums. Across warps, lane partials go through
+// shared memory (two alternating buffers, so one barrier per reduction).
+
+template <typename T>
+__device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(kFull, v, m); }
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(kFull, v, src); }
+
+template <typename T, int NV>
+__device__ __forceinline__ void warp_sum(T (&v)[NV], int lane) {
+    static_assert(NV >= 1 && NV <= 4, "warp_sum handles 1..4 values");
+    if constexpr (NV == 1) {
+        T a = v[0];
+#pragma unroll
+        for (int m = 16; m; m >>= 1) a += shfl_xor(a, m);
+        v[0] = a;
+    } else if constexpr (NV == 2) {
+        const bool hi = lane & 16;
+        T keep = hi ? v[1] : v[0];
+        const T send = hi ? v[0] : v[1];
+        keep += shfl_xor(send, 16);
+#pragma unroll
+        for (int m = 8; m; m >>= 1) keep += shfl_xor(keep, m);
+        v[0] = shfl(keep, 0);
+        v[1] = shfl(keep, 16);
+    } else {
+        const T w3 = (NV == 4) ? v[NV - 1] : T(0);
+        const bool b4 = lane & 16;
+        T k0 = b4 ? v[2] : v[0];
+        T k1 = b4 ? w3 : v[1];
+        const T s0 = b4 ? v[0] : v[2];
+        const T s1 = b4 ? v[1] : w3;
+        k0 += shfl_xor(s0, 16);
+        k1 += shfl_xor(s1, 16);
+        const bool b3 = lane & 8;
+        T keep = b3 ? k1 : k0;
+        const T send = b3 ? k0 : k1;
+        keep += shfl_xor(send, 8);
+#pragma unroll
+        for (int m = 4; m; m >>= 1) keep += shfl_xor(keep, m);
+        v[0] = shfl(keep, 0);
+        v[1] = shfl(keep, 8);
+        v[2] = shfl(keep, 16);
+        if constexpr (NV == 4) v[3] = shfl(keep, 24);
+    }
+}
+
+// red: shared scratch of 2 * 32 * 4 elements; parity alternates per call.
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T* red, int& parity, const Team& tm) {
+    warp_sum<T, NV>(v, tm.lane);
+    if (tm.nwarps == 1) return;
+    T* buf = red + parity * 128;
+    parity ^= 1;
+    if (tm.lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) buf[tm.warp * 4 + j] = v[j];
+    }
+    __syncthreads();
+    if (tm.nwarps <= 4) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            T s = buf[j];
+            for (int w = 1; w < tm.nwarps; ++w) s += buf[w * 4 + j];
+            v[j] = s;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = (tm.lane < tm.nwarps) ? buf[tm.lane * 4 + j] : T(0);
+        warp_sum<T, NV>(v, tm.lane);
+    }
+}
+
+// Partial dot products over the caller's rows (rows beyond n hold zeros).
+template <int R, typename T>
+__device__ __forceinline__ T pdot(const T (&a)[R], const T (&b)[R]) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < R; ++q) s = fma(a[q], b[q], s);
+    return s;
+}
+
+// Write the caller's rows of a register vector to a shared vector.
+template <int R, typename T, typename U>
+__device__ __forceinline__ void put(U* __restrict__ s, const T (&a)[R], const Team& tm, int n) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        if (row < n) s[row] = U(a[q]);
+    }
+}
+
+}  // namespace bbs

@@ -1,0 +1,14 @@
+// cg kernel instantiated for the CSR format, R = 1..kMaxR rows per thread.
+#include "bbs_kernels.h"
+#include "bbs_solvers.cuh"
+
+namespace bbs {
+const void* cg_fn_csr(int R) {
+    static const void* const kTable[kMaxR] = {
+        (const void*)cg_kernel<FMT_CSR, 1>, (const void*)cg_kernel<FMT_CSR, 2>,
+        (const void*)cg_kernel<FMT_CSR, 3>, (const void*)cg_kernel<FMT_CSR, 4>,
+        (const void*)cg_kernel<FMT_CSR, 5>, (const void*)cg_kernel<FMT_CSR, 6>,
+        (const void*)cg_kernel<FMT_CSR, 7>, (const void*)cg_kernel<FMT_CSR, 8>};
+    return kTable[R - 1];
+}
+}  // namespace bbs

@@ -1,0 +1,32 @@
+// Kernel tables: one instantiation per (format, rows per thread R = 1..kMaxR).
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+namespace bbs {
+
+constexpr int kMaxR = 8;
+
+// Largest block a kernel with R rows per thread is compiled for. The bound
+// sets the register budget (65536 / threads, with one block per SM assumed):
+// 64 registers hold one row of every working vector, 128 hold R <= 4, 255
+// hold R <= 8. The largest system is therefore 2048 rows (the paper targets
+// 10 to 2,000 rows, Sec. 2.1).
+__host__ __device__ constexpr int max_threads_for(int R) { return R <= 1 ? 1024 : R <= 4 ? 512 : 256; }
+constexpr int kMaxRows = 2048;
+
+#define BBS_DECL(S)                  \
+    const void* S##_fn(int fmt, int R);  \
+    const void* S##_fn_csr(int R);       \
+    const void* S##_fn_ell(int R);       \
+    const void* S##_fn_dense(int R);
+BBS_DECL(bicgstab)
+BBS_DECL(cg)
+BBS_DECL(gmres)
+BBS_DECL(refine)
+#undef BBS_DECL
+
+cudaError_t launch_convert_f32(const double* src, float* dst, size_t count, cudaStream_t stream);
+
+}  // namespace bbs

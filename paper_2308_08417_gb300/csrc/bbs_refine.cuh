@@ -1,0 +1,160 @@
+// Mixed-precision iterative refinement, fused in one kernel per batch.
+//
+// The paper makes the arithmetic precision a dispatch parameter of the
+// solver kernel (Sec. 3.3-3.4) and notes that iteration counts depend on the
+// precision used (Sec. 2.1). Here the outer loop keeps the residual
+// r = b - A x, its norm, the exit test and the update x += ||r|| d in FP64,
+// and the correction d solves A32 d = r/||r|| by BiCGSTAB + Jacobi entirely
+// in FP32 (values, vectors, reductions), to a relative inner tolerance.
+#pragma once
+
+#include "bbs_solvers.cuh"
+
+namespace bbs {
+
+// FP32 BiCGSTAB from d = 0 on A32 d = w; stops when the recursive residual
+// passes inner_tol*||w||, on a breakdown or non-finite scalar, or after
+// max_inner iterations. Returns the iteration at which it stopped.
+template <int FMT, int R>
+__device__ __forceinline__ int inner_bicgstab32(const Op<FMT, R, float, float>& op,
+                                                const float (&dinv)[R], const float (&w)[R],
+                                                float (&d)[R], float inner_tol, int max_inner,
+                                                float* xa, float* xb, float* red, int& parity,
+                                                const Team& tm, int n) {
+    float r[R], rh[R], p[R], v[R], t[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        d[q] = 0.0f;
+        r[q] = w[q];
+        rh[q] = w[q];
+        p[q] = 0.0f;
+        v[q] = 0.0f;
+    }
+    float s0[1] = {pdot(w, w)};
+    block_sum(s0, red, parity, tm);
+    const float tau2 = inner_tol * inner_tol * s0[0];
+    float rho = s0[0], rho_old = 1.0f, alpha = 1.0f, omega = 1.0f;
+    for (int it = 1; it <= max_inner; ++it) {
+        if (!finite(rho) || rho == 0.0f) return it;
+        const float beta = (rho * alpha) / (rho_old * omega);
+#pragma unroll
+        for (int q = 0; q < R; ++q) p[q] = fmaf(beta, fmaf(-omega, v[q], p[q]), r[q]);
+        {
+            float ph[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) ph[q] = dinv[q] * p[q];
+            put(xa, ph, tm, n);
+        }
+        tm.sync();
+        op.apply(xa, v, tm);
+        float s1[1] = {pdot(rh, v)};
+        block_sum(s1, red, parity, tm);
+        const float sigma = s1[0];
+        if (!finite(sigma) || sigma == 0.0f) return it;
+        alpha = rho / sigma;
+#pragma unroll
+        for (int q = 0; q < R; ++q) r[q] = fmaf(-alpha, v[q], r[q]);
+        {
+            float sh[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) sh[q] = dinv[q] * r[q];
+            put(xb, sh, tm, n);
+        }
+        tm.sync();
+        op.apply(xb, t, tm);
+        float s3[3] = {pdot(r, r), pdot(t, t), pdot(t, r)};
+        block_sum(s3, red, parity, tm);
+        if (s3[0] <= tau2) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int row = tm.row(q);
+                if (row < n) d[q] = fmaf(alpha, xa[row], d[q]);
+            }
+            return it;
+        }
+        omega = (s3[1] == 0.0f) ? 0.0f : s3[2] / s3[1];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int row = tm.row(q);
+            if (row < n) d[q] = fmaf(omega, xb[row], fmaf(alpha, xa[row], d[q]));
+            r[q] = fmaf(-omega, t[q], r[q]);
+        }
+        float s2[2] = {pdot(r, r), pdot(rh, r)};
+        block_sum(s2, red, parity, tm);
+        if (!finite(s2[0]) || s2[0] <= tau2 || omega == 0.0f) return it;
+        rho_old = rho;
+        rho = s2[1];
+    }
+    return max_inner;
+}
+
+// Shared memory: red64[256] | xd[n_pad] (FP64) | red32[256] | xa[n_pad] |
+// xb[n_pad] (FP32) | staged FP32 values (optional)
+template <int FMT, int R>
+__global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const SolveParams P) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    const Team tm = Team::make();
+    const int sys = blockIdx.x;
+    const int n = P.n;
+    double* red64 = reinterpret_cast<double*>(raw);
+    double* xd = red64 + 256;
+    float* red32 = reinterpret_cast<float*>(xd + P.n_pad);
+    float* xa = red32 + 256;
+    float* xb = xa + P.n_pad;
+    int par64 = 0, par32 = 0;
+
+    const Mat<double> A64{P.values + (size_t)sys * P.vps, P.row_ptrs, P.cols, n, P.k};
+    const Op<FMT, R, double, double> op64{A64, nullptr};
+    const Mat<float> A32{P.values32 + (size_t)sys * P.vps, P.row_ptrs, P.cols, n, P.k};
+    const float* as = nullptr;
+    if (P.stage) {
+        float* s = reinterpret_cast<float*>(raw + P.stage_off);
+        stage_values(A32.vals, s, P.vps, tm);
+        __syncthreads();
+        as = s;
+    }
+    const Op<FMT, R, float, float> op32{A32, as};
+
+    double b[R], x[R], r[R];
+    float dinv[R], w[R], d[R];
+    load_system<FMT, R>(P, sys, b, x, tm);
+    jacobi_setup<FMT, R>(A32, P.precond == 1, dinv, tm);
+
+    double s0[1] = {pdot(b, b)};
+    block_sum(s0, red64, par64, tm);
+    const double nb2 = s0[0];
+    if (!finite(nb2)) {
+        write_result(P, sys, x, ST_NAN, 0, __longlong_as_double(0x7ff8000000000000LL), 0, tm);
+        return;
+    }
+    if (nb2 == 0.0) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = 0.0;
+        write_result(P, sys, x, ST_CONVERGED, 0, 0.0, 0, tm);
+        return;
+    }
+    const double tau2 = (P.tol_type == 1) ? P.tol * P.tol * nb2 : P.tol * P.tol;
+    int status = -1, k = 0, inner_total = 0;
+    double rr = 0.0;
+    for (k = 0;; ++k) {
+        rr = true_residual(op64, b, x, r, xd, red64, par64, tm, n);
+        if (!finite(rr)) { status = ST_NAN; break; }
+        if (rr <= tau2) { status = ST_CONVERGED; break; }
+        if (k >= P.max_outer) { status = ST_MAX_ITER; break; }
+        const double rn = sqrt(rr);
+        const double rinv = 1.0 / rn;
+#pragma unroll
+        for (int q = 0; q < R; ++q) w[q] = (float)(r[q] * rinv);
+        inner_total += inner_bicgstab32(op32, dinv, w, d, (float)P.inner_tol, P.max_iters, xa, xb,
+                                        red32, par32, tm, n);
+#pragma unroll
+        for (int q = 0; q < R; ++q) x[q] = fma(rn, (double)d[q], x[q]);
+    }
+    write_result(P, sys, x, status, k, sqrt(rr / nb2), inner_total, tm);
+}
+
+// FP32 copy of the values for the mixed mode (when the caller gives none).
+__global__ void convert_f32_kernel(const double* __restrict__ src, float* __restrict__ dst,
+                                   size_t count);
+
+}  // namespace bbs
