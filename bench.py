@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="scale", choices=["scale", "mixed"])
+    p.add_argument("--systems", type=int, default=0,
+                   help="solve only the first N systems of the workload (profiling runs)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -178,6 +180,9 @@ def main():
     _build.build()
 
     wl, fmt, extra = workload(args.workload)
+    if args.systems:
+        wl = W.Workload(f"{wl.name}[:{args.systems}]", wl.pattern, wl.csr_values[:args.systems],
+                        wl.b[:args.systems], wl.x0[:args.systems])
     A = wl.matrix(fmt)
     dev = torch.device("cuda", local)
     dA = bbs.DeviceBatch.from_batch(A, dev)
