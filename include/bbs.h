@@ -153,6 +153,28 @@ bbs_status bbs_solve_host(bbs_handle *handle, const bbs_batch_matrix *A_host,
                           const double *b_host, double *x_host, const bbs_options *opts,
                           const bbs_log *log_host);
 
+/* bbs_solve without any caller workspace and without allocating: for callers
+ * that cannot call cudaMalloc, such as code recording its work into a CUDA
+ * graph under stream capture (allocation cannot be captured), latency-critical
+ * loops that must not touch the allocator, and hosts that keep device memory
+ * under their own pool or budget. The paper has no counterpart: it is an
+ * interface addition of this library.
+ * Arguments and results are those of bbs_solve (all DEVICE pointers, x in/out,
+ * asynchronous on `stream`). The scratch bbs_solve would take from the
+ * workspace (the FP32 copy of the values in mixed mode, the GMRES basis when it
+ * does not fit in shared memory) comes instead from one static 64 MiB device
+ * array inside the library, which every GPU that loads the library keeps until
+ * the process exits. A batch whose scratch exceeds 64 MiB is solved in
+ * consecutive chunks of systems on `stream`; a single system needing more than
+ * 64 MiB is rejected with BBS_ERR_UNSUPPORTED. The first call on a device looks
+ * up the array's device address, so make that call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller. Calls no cudaMalloc, cudaFree or allocating library routine. */
+bbs_status bbs_solve_noalloc(bbs_handle *handle, const bbs_batch_matrix *A, const double *b,
+                             double *x, const bbs_options *opts, const bbs_log *log,
+                             void *stream);
+
 /* Threads per system by the rule of Sec. 3.6: at least n, a multiple of the
  * warp size 32, at most `max_threads` (the device maximum, 1024 on GB300).
  * Returns 0 for n <= 0 or max_threads < 32. Host only. */

@@ -65,6 +65,8 @@ def lib():
                                 P(bbs_options), P(bbs_log), C.c_void_p, C.c_size_t, C.c_void_p]
         L.bbs_solve_host.argtypes = [C.c_void_p, P(bbs_batch_matrix), C.c_void_p, C.c_void_p,
                                      P(bbs_options), P(bbs_log)]
+        L.bbs_solve_noalloc.argtypes = [C.c_void_p, P(bbs_batch_matrix), C.c_void_p, C.c_void_p,
+                                        P(bbs_options), P(bbs_log), C.c_void_p]
         L.bbs_paper_block_size.argtypes = [C.c_int32, C.c_int32]
         L.bbs_paper_block_size.restype = C.c_int32
         L.bbs_default_block_size.argtypes = [C.c_int32, C.c_int32]
@@ -72,7 +74,7 @@ def lib():
         L.bbs_last_error.restype = C.c_char_p
         L.bbs_version.restype = C.c_char_p
         for name in ("bbs_default_options", "bbs_create", "bbs_destroy", "bbs_workspace_size",
-                     "bbs_solve", "bbs_solve_host"):
+                     "bbs_solve", "bbs_solve_host", "bbs_solve_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -222,6 +224,16 @@ class Handle:
         st = stream if stream is not None else torch.cuda.current_stream(A.values.device)
         _check(lib().bbs_solve(self._h, C.byref(s), _ptr(b), _ptr(x), C.byref(opts), C.byref(lg),
                                _ptr(workspace), ws_bytes, C.c_void_p(st.cuda_stream)), "bbs_solve")
+
+    def solve_noalloc(self, A: DeviceBatch, b: torch.Tensor, x: torch.Tensor, opts: bbs_options,
+                      log: Log, stream=None):
+        """bbs_solve_noalloc: like solve() with the library's static scratch
+        instead of a workspace (for callers that cannot allocate)."""
+        s = A.struct()
+        lg = log.struct()
+        st = stream if stream is not None else torch.cuda.current_stream(A.values.device)
+        _check(lib().bbs_solve_noalloc(self._h, C.byref(s), _ptr(b), _ptr(x), C.byref(opts),
+                                       C.byref(lg), C.c_void_p(st.cuda_stream)), "bbs_solve_noalloc")
 
     def solve_host(self, A: DeviceBatch, b: torch.Tensor, x: torch.Tensor, opts: bbs_options,
                    log: Log):

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/bbs.h"
+#include "bbs_internal.h"
 #include "bbs_kernels.h"
 #include "bbs_params.h"
 
@@ -174,6 +175,11 @@ cudaError_t allow_smem(const void* fn, size_t smem) {
 }
 
 }  // namespace
+
+namespace bbs {
+bbs_status record_error(bbs_status s, const char* msg) { return fail(s, "%s", msg); }
+int handle_device(const bbs_handle* h) { return h->device; }
+}  // namespace bbs
 
 extern "C" {
 
