@@ -1,13 +1,19 @@
 """Benchmark: systems solved per second to relative residual 1e-10.
 
-Default workload: 65,536 nonsymmetric 5-point-stencil systems on a 12x12 grid
-(n = 144, nnz = 672), BatchCsr FP64, BiCGSTAB + scalar Jacobi, relative
-tolerance 1e-10, max 500 iterations, x0 = 0. One step = one bbs_solve over
-the whole batch (one kernel launch). Inputs (352 MB of values) exceed L2
-(129 MB), so no flush is needed between steps.
+Headline workload (default, --workload scale): 65,536 nonsymmetric
+5-point-stencil systems on a 12x12 grid (n = 144, nnz = 672), BatchCsr FP64,
+BiCGSTAB + scalar Jacobi, relative tolerance 1e-10, max 500 iterations,
+x0 = 0. One step = one bbs_solve over the whole batch (one kernel launch).
+Its inputs (352 MB of values) exceed L2 (129 MB), so no flush is needed.
+
+Other workloads (--workload): mixed (16,384 9-point systems, n = 1024, ELL;
+FP32-inner / FP64-outer refinement against plain FP64 BiCGSTAB) and uneven
+(100,000 systems, n log-uniform in [16, 1024], one persistent graph launch
+with autotuned team sizes). The default line carries short measurements of
+these under "extras".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload scale|mixed]
+                  [--workload scale|mixed|uneven] [--systems N] [--no-extras]
 
 --impl reference times the CPU oracle (plain C, OpenMP) on a bounded sample
 of the same workload, on the host cores.
@@ -37,12 +43,15 @@ METRIC = "systems solved/s to rel. residual 1e-10"
 # FP64 throughput of one GB300 SM per clock (FLOP/clk/SM, FMA = 2), from the
 # nominal 1.25 TFLOP/s at 2,070 MHz over 152 SMs: 1.25e12 / (152 * 2.07e9) = 3.97.
 FP64_FLOP_PER_CLK_SM = 4.0
+# FP32 (non-tensor) FMA lanes: 128 per SM per clock = 256 FLOP/clk/SM.
+FP32_FLOP_PER_CLK_SM = 256.0
 NUM_SMS = 152
+HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 
-# dram bytes (read + write) per launch of the dominant kernel from an ncu
-# capture of this kernel (profiles/bicgstab_kernel_stencil2d5_n144.md: 280.0 MB
-# for 32,768 systems, scaled by 2 to the 65,536-system launch); an entry is
-# removed when its kernel changes.
+# dram bytes (read + write) per launch of a kernel from an ncu capture of it,
+# scaled to the benchmark's launch; an entry is removed when its kernel changes.
+# bicgstab_kernel: profiles/bicgstab_kernel_stencil2d5_n144.md, 280.0 MB for
+# 32,768 systems -> 560 MB for the 65,536-system launch.
 TRAFFIC_BYTES = {"bicgstab_kernel": 560.0e6}
 
 
@@ -52,21 +61,16 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="scale", choices=["scale", "mixed"])
+    p.add_argument("--workload", default="scale", choices=["scale", "mixed", "uneven", "learned"])
     p.add_argument("--systems", type=int, default=0,
                    help="solve only the first N systems of the workload (profiling runs)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-extras", action="store_true")
     return p.parse_args()
 
 
-def workload(name):
-    if name == "mixed":
-        wl = W.mixed_precision()
-        return wl, "ell", dict(precision="mixed", inner_tol=1e-4, max_iters=200, max_outer=30)
-    wl = W.plain_at_scale()
-    return wl, "csr", dict()
-
+# --------------------------------------------------------------- clocks
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
@@ -78,6 +82,7 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
+        self.out = ""
 
     def __enter__(self):
         try:
@@ -90,7 +95,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -111,24 +115,290 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_run(A, b, threads, opts, budget_s=10.0):
-    """Oracle on whole-batch passes until ~budget_s of CPU time; systems/s."""
-    import oracle
+# ------------------------------------------------------------ workloads
 
-    kw = dict(max_iters=opts.get("max_iters", 500))
-    t0 = time.perf_counter()
-    done = 0
-    while True:
-        if opts.get("precision") == "mixed":
-            oracle.refine(A, b, inner_tol=opts["inner_tol"], max_inner=opts["max_iters"],
-                          max_outer=opts["max_outer"], threads=threads)
-        else:
-            oracle.solve_batch(A, b, threads=threads, **kw)
-        done += A.num_batch
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    return done / (time.perf_counter() - t0), done
+def subset_workload(wl, k):
+    if not k:
+        return wl
+    return W.Workload(f"{wl.name}[:{k}]", wl.pattern, wl.csr_values[:k], wl.b[:k], wl.x0[:k])
 
+
+class Uniform:
+    """bbs_solve over a shared-pattern batch (one launch per step)."""
+
+    def __init__(self, bbs, torch, dev, wl, fmt, opts_kw, label):
+        self.bbs, self.torch, self.dev = bbs, torch, dev
+        self.wl, self.fmt, self.label = wl, fmt, label
+        self.A = wl.matrix(fmt)
+        self.dA = bbs.DeviceBatch.from_batch(self.A, dev)
+        self.b = torch.as_tensor(wl.b, device=dev)
+        self.x0 = torch.as_tensor(wl.x0, device=dev)
+        self.x = self.x0.clone()
+        self.h = bbs.Handle(dev.index or 0)
+        self.opts = bbs.bbs_default_options(**opts_kw)
+        self.mixed = self.opts.precision == 1
+        self.log = bbs.Log.empty(wl.num_batch, device=dev, inner=self.mixed)
+        self.ws = self.h.workspace(self.dA, self.opts)
+        self.num_batch = wl.num_batch
+        self.kernel = "refine_kernel" if self.mixed else "bicgstab_kernel"
+        self.launches_per_step = 2 if (self.mixed and self.ws is not None) else 1
+
+    def reset(self):
+        self.x.copy_(self.x0)
+
+    def step(self, stream):
+        self.h.solve(self.dA, self.b, self.x, self.opts, self.log, self.ws, stream)
+
+    def work(self):
+        """(algorithmic FLOPs of the last solve, arithmetic) per launch."""
+        A = self.A
+        per_it = 4 * A.nnz + 26 * A.n
+        if self.mixed:
+            inner = self.log.inner_iters.cpu().numpy().astype(np.int64)
+            return float(inner.sum()) * per_it, "fp32"
+        it = self.log.iters.cpu().numpy().astype(np.int64)
+        return float(it.sum()) * per_it, "fp64"
+
+    def compulsory_bytes(self):
+        B, A = self.num_batch, self.A
+        return 8 * (B * A.values.shape[1] + 3 * B * A.n) + 16 * B
+
+    def summary(self):
+        it = self.log.iters.cpu().numpy()
+        st = self.log.status.cpu().numpy()
+        out = {"mean": float(it.mean()), "max": int(it.max()), "converged": int((st == 0).sum())}
+        if self.mixed:
+            out["inner_mean"] = float(self.log.inner_iters.cpu().numpy().mean())
+        return out
+
+    def e2e(self, reps):
+        bbs, torch = self.bbs, self.torch
+        hA = bbs.DeviceBatch.from_batch(self.A, "cpu", pin=True)
+        hb = torch.as_tensor(self.wl.b).pin_memory()
+        hx0 = torch.as_tensor(self.wl.x0).pin_memory()
+        hx = hx0.clone().pin_memory()
+        hlog = bbs.Log.empty(self.num_batch, device="cpu", pin=True, inner=self.mixed)
+        self.h.solve_host(hA, hb, hx, self.opts, hlog)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            hx.copy_(hx0)
+            self.h.solve_host(hA, hb, hx, self.opts, hlog)
+        dt = (time.perf_counter() - t0) / reps
+        h2d = (hA.values.numel() * 8 + (hA.row_ptrs.numel() * 4 if hA.row_ptrs is not None else 0)
+               + (hA.col_idxs.numel() * 4 if hA.col_idxs is not None else 0) + 2 * hb.numel() * 8)
+        d2h = hx.numel() * 8 + self.num_batch * (4 + 8 + 4 + (4 if self.mixed else 0))
+        return {"value": self.num_batch / dt, "unit": "systems/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "path": "bbs_solve_host (host buffers)"}
+
+    def cpu(self, threads, budget_s):
+        import oracle
+
+        k = min(8192 if not self.mixed else 256, self.num_batch)
+        As, bs = self.A.subset(np.arange(k)), self.wl.b[:k]
+        t0 = time.perf_counter()
+        done = 0
+        while True:
+            if self.mixed:
+                oracle.refine(As, bs, inner_tol=self.opts.inner_tol, max_inner=self.opts.max_iters,
+                              max_outer=self.opts.max_outer, threads=threads)
+            else:
+                oracle.solve_batch(As, bs, max_iters=self.opts.max_iters, threads=threads)
+            done += As.num_batch
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        return (done / (time.perf_counter() - t0),
+                f"first {As.num_batch} systems of {self.wl.name}, repeated to {done} solves")
+
+
+class Uneven:
+    """One graph launch of the persistent uneven-batch plan per step."""
+
+    def __init__(self, bbs, torch, dev, vb, tune=True):
+        self.bbs, self.torch, self.dev, self.vb = bbs, torch, dev, vb
+        self.label = vb.name
+        self.vbd = bbs.VarDeviceBatch.from_varbatch(vb, dev)
+        self.b = torch.as_tensor(vb.b, device=dev)
+        self.x0 = torch.as_tensor(vb.x0, device=dev)
+        self.x = self.x0.clone()
+        self.h = bbs.Handle(dev.index or 0)
+        self.opts = bbs.bbs_default_options()
+        t0 = time.perf_counter()
+        self.tuning = (bbs.bbs_var_tune(self.h, self.vbd, self.b, self.x0, self.opts, sample=512)
+                       if tune else None)
+        self.tune_s = time.perf_counter() - t0
+        self.plan = bbs.VarPlan(self.h, self.vbd, self.opts, self.tuning)
+        self.log = bbs.Log.empty(vb.num_batch, device=dev)
+        self.num_batch = vb.num_batch
+        self.kernel = "varsize_kernel"
+        self.launches_per_step = 1
+        self.mixed = False
+
+    def reset(self):
+        self.x.copy_(self.x0)
+
+    def step(self, stream):
+        self.plan.solve(self.b, self.x, self.log, stream)
+
+    def work(self):
+        it = self.log.iters.cpu().numpy().astype(np.int64)
+        per_it = 4 * self.vb.sys_nnz().astype(np.int64) + 26 * self.vb.sys_n().astype(np.int64)
+        return float((it * per_it).sum()), "fp64"
+
+    def compulsory_bytes(self):
+        return 8 * (self.vb.values.size + 3 * self.vb.b.size) + 16 * self.num_batch
+
+    def summary(self):
+        it = self.log.iters.cpu().numpy()
+        st = self.log.status.cpu().numpy()
+        return {"mean": float(it.mean()), "max": int(it.max()), "converged": int((st == 0).sum()),
+                "tuning": self.tuning.as_dict() if self.tuning is not None else "default",
+                "tune_s": self.tune_s}
+
+    def e2e(self, reps):
+        torch = self.torch
+        hb = torch.as_tensor(self.vb.b).pin_memory()
+        hv = torch.as_tensor(self.vb.values).pin_memory()
+        hx0 = torch.as_tensor(self.vb.x0).pin_memory()
+        hx = hx0.clone().pin_memory()
+        hit = torch.empty(self.num_batch, dtype=torch.int32).pin_memory()
+        vals = self.vbd.tensors["values"]
+        stream = torch.cuda.current_stream(self.dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            vals.copy_(hv, non_blocking=True)
+            self.b.copy_(hb, non_blocking=True)
+            self.x.copy_(hx0, non_blocking=True)
+            self.plan.solve(self.b, self.x, self.log, stream)
+            hx.copy_(self.x, non_blocking=True)
+            hit.copy_(self.log.iters, non_blocking=True)
+            torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        return {"value": self.num_batch / dt, "unit": "systems/s",
+                "h2d_bytes_per_step": hv.numel() * 8 + 2 * hb.numel() * 8,
+                "d2h_bytes_per_step": hx.numel() * 8 + self.num_batch * 4,
+                "path": "host copies + bbs_var_solve (graph launch)"}
+
+    def cpu(self, threads, budget_s):
+        import oracle
+
+        sel = np.arange(0, self.num_batch, 10)
+        t0 = time.perf_counter()
+        done = 0
+        while True:
+            oracle.solve_varsize(self.vb, systems=sel, threads=threads)
+            done += len(sel)
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        return (done / (time.perf_counter() - t0),
+                f"every 10th system of {self.vb.name}, repeated to {done} solves")
+
+
+def make_runner(name, bbs, torch, dev, systems=0):
+    if name == "mixed":
+        wl = subset_workload(W.mixed_precision(), systems)
+        # inner tolerance 1e-2: the fastest of 0.3 / 0.1 / 0.03 / 1e-2 / 1e-3 / 1e-4 in a sweep
+        return Uniform(bbs, torch, dev, wl, "ell",
+                       dict(precision="mixed", inner_tol=1e-2, max_iters=200, max_outer=30), wl.name)
+    if name == "mixed_fp64":
+        wl = subset_workload(W.mixed_precision(), systems)
+        return Uniform(bbs, torch, dev, wl, "ell", dict(max_iters=2000), wl.name)
+    if name == "uneven":
+        return Uneven(bbs, torch, dev, W.uneven(systems or 100000))
+    wl = subset_workload(W.plain_at_scale(), systems)
+    return Uniform(bbs, torch, dev, wl, "csr", {}, wl.name)
+
+
+def learned_run(bbs, torch, dev, eval_steps=192, num_batch=16384):
+    """Time-stepped batch: train on steps 0..63, then per step time (MLP
+    prediction + solve) against (solve from x(t-1))."""
+    from paper_2308_08417_gb300.learned import TimeStepped
+
+    ts = W.time_stepped(num_batch=num_batch, steps=64 + eval_steps)
+    run = TimeStepped(ts, device=str(dev), hidden=256, seed=0, max_batch=4096)
+    rep = run.run(train_steps=64, eval_steps=eval_steps, epochs=6, batch=4096)
+    s = rep.summary()
+    s["workload"] = f"timestepped_stencil2d5_12x12_B{num_batch}_T{64 + eval_steps}"
+    return s
+
+
+def time_steps(r, torch, stream, steps, warmup, dist=None, sample_clocks=False, dev_index=0):
+    for _ in range(max(warmup, 3)):
+        r.reset()
+        r.step(stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev_index) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    t0.record(stream)
+    for k in range(steps):
+        r.reset()
+        ev[k][0].record(stream)
+        r.step(stream)
+        ev[k][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    total_ms = t0.elapsed_time(t1)
+    solve_ms = [a.elapsed_time(z) for a, z in ev]
+    return total_ms, solve_ms, (clk.summary() if clk else None)
+
+
+def roofline(r, solve_ms, mhz):
+    flops, arith = r.work()
+    avg_s = statistics.mean(solve_ms) / 1e3
+    per_clk = FP64_FLOP_PER_CLK_SM if arith == "fp64" else FP32_FLOP_PER_CLK_SM
+    peak = per_clk * NUM_SMS * mhz * 1e6 / 1e12
+    achieved = flops / avg_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get(r.kernel), "kernel": r.kernel,
+            "arith": arith,
+            "peak_source": f"{arith.upper()} {per_clk:g} FLOP/clk/SM x {NUM_SMS} SMs x median SM clock {mhz:.0f} MHz"}
+
+
+def extras(bbs, torch, dev, stream, mhz):
+    """Short measurements of the other forms on the same GPU."""
+    out = {}
+    try:
+        f64 = make_runner("mixed_fp64", bbs, torch, dev)
+        tot64, ms64, _ = time_steps(f64, torch, stream, 3, 1)
+        mix = make_runner("mixed", bbs, torch, dev)
+        tot, ms, _ = time_steps(mix, torch, stream, 5, 2)
+        v64 = f64.num_batch * 3 / (tot64 / 1e3)
+        vm = mix.num_batch * 5 / (tot / 1e3)
+        x64 = f64.x.cpu().numpy()
+        xm = mix.x.cpu().numpy()
+        err = float((np.linalg.norm(xm - x64, axis=1) / np.linalg.norm(x64, axis=1)).max())
+        out["mixed"] = {"workload": mix.label, "value": vm, "fp64_value": v64, "unit": "systems/s",
+                        "speedup_vs_fp64": vm / v64, "max_rel_diff_vs_fp64": err,
+                        "iterations": mix.summary(), "fp64_iterations": f64.summary(),
+                        "roofline": roofline(mix, ms, mhz), "fp64_roofline": roofline(f64, ms64, mhz)}
+        del f64, mix
+    except Exception as e:  # report, do not hide
+        out["mixed"] = {"error": repr(e)}
+    try:
+        out["learned"] = learned_run(bbs, torch, dev, eval_steps=32)
+    except Exception as e:
+        out["learned"] = {"error": repr(e)}
+    try:
+        un = make_runner("uneven", bbs, torch, dev)
+        tot, ms, _ = time_steps(un, torch, stream, 5, 2)
+        out["uneven"] = {"workload": un.label, "value": un.num_batch * 5 / (tot / 1e3),
+                         "unit": "systems/s", "iterations": un.summary(),
+                         "roofline": roofline(un, ms, mhz), "launches_per_step": "1 graph (memset + kernel)"}
+        del un
+    except Exception as e:
+        out["uneven"] = {"error": repr(e)}
+    return out
+
+
+# ---------------------------------------------------------- reference arm
 
 def reference_arm(args, rank):
     """The CPU oracle as the reference arm (rank 0 only)."""
@@ -136,29 +406,45 @@ def reference_arm(args, rank):
         return
     import oracle
 
-    wl, fmt, opts = workload(args.workload)
-    A = wl.matrix(fmt)
-    sample = 8192 if args.workload == "scale" else 512
-    As, bs = A.subset(np.arange(sample)), wl.b[:sample]
     threads = oracle.num_threads()
+    if args.workload == "uneven":
+        vb = W.uneven(args.systems or 100000)
+        sel = np.arange(0, vb.num_batch, 10)
+        run = lambda: oracle.solve_varsize(vb, systems=sel, threads=threads)  # noqa: E731
+        sample, name = len(sel), vb.name
+    else:
+        if args.workload == "mixed":
+            wl, fmt, k = W.mixed_precision(), "ell", 512
+        else:
+            wl, fmt, k = W.plain_at_scale(), "csr", 8192
+        A = wl.matrix(fmt)
+        As, bs = A.subset(np.arange(k)), wl.b[:k]
+        if args.workload == "mixed":
+            run = lambda: oracle.refine(As, bs, inner_tol=1e-4, max_inner=200, max_outer=30,  # noqa: E731
+                                        threads=threads)
+        else:
+            run = lambda: oracle.solve_batch(As, bs, threads=threads)  # noqa: E731
+        sample, name = k, wl.name
     for _ in range(args.warmup):
-        cpu_oracle_run(As, bs, threads, opts, budget_s=0.0)
+        run()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        cpu_oracle_run(As, bs, threads, opts, budget_s=0.0)
+        run()
     dt = time.perf_counter() - t0
     value = sample * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "sample_systems": sample},
+            "config": {"workload": name, "sample_systems": sample},
             "cpu_baseline": {"value": value, "unit": "systems/s", "cores": threads, "kind": "oracle",
-                             "sample": f"first {sample} systems of {wl.name}, one pass per step"},
+                             "sample": f"{sample} systems of {name}, one pass per step"},
             "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+# ------------------------------------------------------------------ main
 
 def main():
     args = parse()
@@ -180,119 +466,55 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
-
-    wl, fmt, extra = workload(args.workload)
-    if args.systems:
-        wl = W.Workload(f"{wl.name}[:{args.systems}]", wl.pattern, wl.csr_values[:args.systems],
-                        wl.b[:args.systems], wl.x0[:args.systems])
-    A = wl.matrix(fmt)
     dev = torch.device("cuda", local)
-    dA = bbs.DeviceBatch.from_batch(A, dev)
-    b = torch.as_tensor(wl.b, device=dev)
-    x0 = torch.as_tensor(wl.x0, device=dev)
-    x = x0.clone()
-    h = bbs.Handle(local)
-    opts = bbs.bbs_default_options(**extra)
-    mixed = opts.precision == 1
-    log = bbs.Log.empty(wl.num_batch, device=dev, inner=mixed)
-    ws = h.workspace(dA, opts)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        x.copy_(x0)
-        h.solve(dA, b, x, opts, log, ws, stream)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        t_start.record(stream)
-        for k in range(args.steps):
-            x.copy_(x0)
-            ev[k][0].record(stream)
-            h.solve(dA, b, x, opts, log, ws, stream)
-            ev[k][1].record(stream)
-        t_end.record(stream)
-        torch.cuda.synchronize()
-    total_ms = t_start.elapsed_time(t_end)
-    solve_ms = [a.elapsed_time(z) for a, z in ev]
+    if args.workload == "learned":
+        s = learned_run(bbs, torch, dev, eval_steps=192, num_batch=args.systems or 16384)
+        line = {"metric": METRIC, "value": s["systems_per_s_learned"], "unit": "systems/s",
+                "n_gpus": world, "steps": s["eval_steps"], "warmup": 64,
+                "ms_per_step": 1e3 * s["num_batch"] / s["systems_per_s_learned"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16",
+                "data": "synthetic", "config": {"workload": s["workload"], "train_steps": 64},
+                "gpu_launches": None, "learned": s}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    r = make_runner(args.workload, bbs, torch, dev, args.systems)
+    total_ms, solve_ms, clocks = time_steps(r, torch, stream, args.steps, args.warmup, dist,
+                                            sample_clocks=True, dev_index=local)
     if dist is not None:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    clocks = clk.summary()
-
-    iters = log.iters.cpu().numpy().astype(np.int64)
-    status = log.status.cpu().numpy()
-    B = wl.num_batch
-    value = B * world * args.steps / (total_ms / 1e3)
-    avg_solve_s = statistics.mean(solve_ms) / 1e3
-    if mixed:
-        inner = log.inner_iters.cpu().numpy().astype(np.int64)
-        flops = float(inner.sum()) * (4 * A.nnz + 26 * A.n)
-        bound, unit = "alu", "TFLOP/s"
-    else:
-        flops = float(iters.sum()) * (4 * A.nnz + 26 * A.n)
-        bound, unit = "alu", "TFLOP/s"
     mhz = clocks.get("sm_mhz") or 2070.0
-    peak = FP64_FLOP_PER_CLK_SM * NUM_SMS * mhz * 1e6 / 1e12
-    achieved = flops / avg_solve_s / 1e12
-    kname = "refine_kernel" if mixed else "bicgstab_kernel"
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get(kname),
-                "kernel": kname, "peak_source": f"FP64 {FP64_FLOP_PER_CLK_SM} FLOP/clk/SM x {NUM_SMS} SMs x median SM clock {mhz:.0f} MHz"}
-    hbm_bytes = 8 * (B * A.values.shape[1] + 3 * B * A.n) + 16 * B
-    hbm_gbs = hbm_bytes / avg_solve_s / 1e9
-
+    value = r.num_batch * world * args.steps / (total_ms / 1e3)
+    avg_solve_s = statistics.mean(solve_ms) / 1e3
+    hbm_bytes = r.compulsory_bytes()
     line = {"metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "format": fmt, "solver": "bicgstab+jacobi",
-                       "num_batch_per_gpu": B, "n": A.n, "nnz": A.nnz, "tol": 1e-10,
-                       "l2": "inputs larger than L2 (no flush)"},
-            "gpu_launches": args.steps * (1 + (1 if ws is not None and mixed else 0)),
-            "clocks": clocks, "roofline": roofline,
-            "iterations": {"mean": float(iters.mean()), "max": int(iters.max()),
-                           "converged": int((status == 0).sum())},
-            "compulsory_hbm": {"bytes": hbm_bytes, "GB/s": hbm_gbs,
-                               "frac_of_hbm": hbm_gbs / 6789.0}}
-
+            "dtype": "f64+f32" if r.mixed else "f64", "data": "synthetic",
+            "config": {"workload": r.label, "num_batch_per_gpu": r.num_batch, "tol": 1e-10,
+                       "solver": "bicgstab+jacobi", "l2": "inputs larger than L2 (no flush)"},
+            "gpu_launches": args.steps * r.launches_per_step,
+            "clocks": clocks, "roofline": roofline(r, solve_ms, mhz),
+            "iterations": r.summary(),
+            "compulsory_hbm": {"bytes": hbm_bytes, "GB/s": hbm_bytes / avg_solve_s / 1e9,
+                               "frac_of_hbm": hbm_bytes / avg_solve_s / 1e9 / HBM_GBS}}
     if rank == 0 and not args.no_e2e:
-        hA = bbs.DeviceBatch.from_batch(A, "cpu", pin=True)
-        hb = torch.as_tensor(wl.b).pin_memory()
-        hx0 = torch.as_tensor(wl.x0).pin_memory()
-        hx = hx0.clone().pin_memory()
-        hlog = bbs.Log.empty(B, device="cpu", pin=True, inner=mixed)
-        h.solve_host(hA, hb, hx, opts, hlog)
-        reps = max(2, min(args.steps, 5))
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            hx.copy_(hx0)
-            h.solve_host(hA, hb, hx, opts, hlog)
-        e2e_s = (time.perf_counter() - t0) / reps
-        h2d = (hA.values.numel() * 8 + (hA.row_ptrs.numel() * 4 if hA.row_ptrs is not None else 0)
-               + (hA.col_idxs.numel() * 4 if hA.col_idxs is not None else 0) + 2 * hb.numel() * 8)
-        d2h = hx.numel() * 8 + B * (4 + 8 + 4 + (4 if mixed else 0))
-        line["e2e"] = {"value": B / e2e_s, "unit": "systems/s", "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h}
+        line["e2e"] = r.e2e(max(2, min(args.steps, 5)))
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
 
         threads = oracle.num_threads()
-        sample = 8192 if args.workload == "scale" else 256
-        As, bs = A.subset(np.arange(sample)), wl.b[:sample]
-        v, done = cpu_oracle_run(As, bs, threads, extra, budget_s=10.0)
+        v, sample = r.cpu(threads, 10.0)
         line["cpu_baseline"] = {"value": v, "unit": "systems/s", "cores": threads, "kind": "oracle",
-                                "sample": f"first {sample} systems of {wl.name}, repeated to "
-                                          f"{done} solves (~10 s)"}
+                                "sample": sample + " (~10 s)"}
+    if rank == 0 and world == 1 and args.workload == "scale" and not args.no_extras and not args.systems:
+        del r
+        torch.cuda.empty_cache()
+        line["extras"] = extras(bbs, torch, dev, stream, mhz)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -175,14 +175,166 @@ bbs_status bbs_solve_noalloc(bbs_handle *handle, const bbs_batch_matrix *A, cons
                              double *x, const bbs_options *opts, const bbs_log *log,
                              void *stream);
 
+/* ------------------------------------------------------------------------
+ * Uneven batches: systems of different sizes and patterns in one persistent,
+ * graph-captured launch. The paper's batch shares one pattern (Sec. 3.1) and
+ * tunes launch thresholds per device experimentally (Sec. 3.6); this
+ * extension keeps one thread team per system but lets the team size follow
+ * the system size, chosen per size bucket by a measured autotuner.
+ * ------------------------------------------------------------------------ */
+
+/* Systems of uneven size in BatchCsr: a pool of patterns and one record per
+ * system. All pointers DEVICE. System i uses pattern sys_pattern[i]: its
+ * row_ptrs start at row_ptrs + pat_rp_off[p] (n+1 entries, values relative to
+ * the pattern's first entry), its col_idxs at col_idxs + pat_ci_off[p]; its
+ * values start at values + val_off[i] (pat_nnz[p] entries) and its vectors
+ * at b + vec_off[i], x + vec_off[i] (pat_n[p] entries). */
+typedef struct {
+    int32_t num_batch;
+    int32_t num_patterns;
+    const int32_t *pat_n;
+    const int32_t *pat_nnz;
+    const int64_t *pat_rp_off;
+    const int64_t *pat_ci_off;
+    const int32_t *row_ptrs;
+    const int32_t *col_idxs;
+    const int32_t *sys_pattern;
+    const int64_t *val_off;
+    const int64_t *vec_off;
+    const double *values;
+} bbs_var_batch;
+
+/* HOST copies of the metadata the planner reads: pat_n and pat_nnz
+ * [num_patterns], sys_pattern [num_batch]. */
+typedef struct {
+    const int32_t *pat_n;
+    const int32_t *pat_nnz;
+    const int32_t *sys_pattern;
+} bbs_var_host_info;
+
+/* Launch choices for an uneven batch. Systems fall in size buckets
+ * (bucket b holds n <= bucket_max_n[b], ascending); each bucket has the number
+ * of warps that solve one of its systems (1, 2, 4, 8 or 16; at most
+ * block_warps) and whether its systems' values are staged in shared memory.
+ * block_warps is 8 (up to 8 rows per thread) or 16 (up to 4 rows per thread).
+ * The planner lowers a bucket's warps to those of the next larger bucket if
+ * they exceed them and raises them to the minimum its rows need. */
+typedef struct {
+    int32_t num_buckets; /* 1..8 */
+    int32_t bucket_max_n[8];
+    int32_t team_warps[8];
+    int32_t stage_values[8];
+    int32_t block_warps;
+    int32_t reserved;
+} bbs_var_tuning;
+
+typedef struct bbs_var_plan bbs_var_plan;
+
+/* Default tuning: power-of-two buckets up to max_n, one warp per 5 rows per
+ * thread (as bbs_default_block_size), values streamed, 8-warp blocks. Host only. */
+bbs_status bbs_var_default_tuning(int32_t max_n, bbs_var_tuning *tuning);
+
+/* Plan the persistent solve of `batch` (FP64, BiCGSTAB or CG, Jacobi or
+ * none): order the systems longest first, group them in segments of equal
+ * team size, size the grid to fill every SM and capture "reset the work
+ * counters + one persistent launch" in a CUDA graph. Allocates the plan's own
+ * device buffers (system order, counters). tuning NULL = default tuning. */
+bbs_status bbs_var_plan_create(bbs_handle *handle, const bbs_var_batch *batch,
+                               const bbs_var_host_info *host, const bbs_options *opts,
+                               const bbs_var_tuning *tuning, bbs_var_plan **plan);
+
+/* Run a plan: one graph launch on `stream`. b, x (in: x0, out: solution) are
+ * DEVICE arrays laid out by vec_off; log is DEVICE (inner_iters unused).
+ * Asynchronous. Plans of the same handle must not run concurrently. */
+bbs_status bbs_var_solve(bbs_var_plan *plan, const double *b, double *x, const bbs_log *log,
+                         void *stream);
+
+/* Release a plan (waits for its graph to finish). NULL is accepted. */
+bbs_status bbs_var_plan_destroy(bbs_var_plan *plan);
+
+/* Autotuner: for every size bucket that holds systems, time the persistent
+ * kernel on a sample of the bucket's systems (at least `sample`, and at least
+ * four times the systems the GPU holds at once, so that each trial measures
+ * throughput; all of them when the bucket is smaller) for each team
+ * size and staging choice (and both block shapes), and write the fastest
+ * choices to *tuning. b and x0 are DEVICE arrays of the batch; x0 is not
+ * modified (trials run on a private copy). Synchronous; allocates and frees
+ * its own scratch. */
+bbs_status bbs_var_tune(bbs_handle *handle, const bbs_var_batch *batch,
+                        const bbs_var_host_info *host, const double *b, const double *x0,
+                        const bbs_options *opts, int32_t sample, bbs_var_tuning *tuning);
+
+/* ------------------------------------------------------------------------
+ * Learned initial guess for time-stepped batches (an extension: the paper
+ * motivates it with the solver's use of an initial guess, Sec. 2.1). A small
+ * MLP predicts each system's change of solution from its diagonal, its
+ * right-hand side and its previous solution: 3n standardised inputs ->
+ * hidden -> hidden -> hidden -> n, GELU (tanh form) after each hidden layer,
+ * BF16 tensor-core GEMMs with FP32 accumulation, FP32 master weights, Adam
+ * (beta 0.9 / 0.999, eps 1e-8), mean-squared-error loss on the standardised
+ * change. The solver itself is unchanged: it still iterates to its tolerance
+ * from whatever guess it is given.
+ * Parameter layout (FP32, flat): W1 b1 W2 b2 W3 b3 W4 b4, W_l row-major
+ * [out, in] (y = x W^T + b); W1 is [hidden, 3n], W4 is [n, hidden].
+ * Feature rows (BF16, stored as uint16_t) have ceil(3n/32)*32 columns:
+ * standardised diag(A) (n), b (n), x_prev (n), then zeros.
+ * ------------------------------------------------------------------------ */
+typedef struct bbs_mlp bbs_mlp;
+
+/* Create a network for systems of n rows (1..2048) with `hidden` units (a
+ * multiple of 32, 32..4096) and minibatches of up to max_batch rows (a
+ * multiple of 32). Weights are drawn from U(-1/sqrt(in), 1/sqrt(in)) by a
+ * counter-based hash of `seed` (output layer scaled by 0.1), biases zero.
+ * Allocates all its device buffers here. */
+bbs_status bbs_mlp_create(bbs_handle *handle, int32_t n, int32_t hidden, uint64_t seed,
+                          int32_t max_batch, bbs_mlp **mlp);
+bbs_status bbs_mlp_destroy(bbs_mlp *mlp);
+/* Number of FP32 parameters (length of the flat layout). */
+bbs_status bbs_mlp_param_count(const bbs_mlp *mlp, int64_t *count);
+/* Copy the FP32 master parameters to / from a DEVICE array (set also
+ * refreshes the BF16 copies). Asynchronous on stream. */
+bbs_status bbs_mlp_get_params(bbs_mlp *mlp, float *params, void *stream);
+bbs_status bbs_mlp_set_params(bbs_mlp *mlp, const float *params, void *stream);
+/* Accumulate the input and target moments of one time step: A (DEVICE
+ * BatchCsr with this network's n), b, x_prev, x_next (DEVICE, num_batch*n). */
+bbs_status bbs_mlp_observe(bbs_mlp *mlp, const bbs_batch_matrix *A, const double *b,
+                           const double *x_prev, const double *x_next, void *stream);
+/* Turn the accumulated moments into the standardisation (mean, std). */
+bbs_status bbs_mlp_finalize_stats(bbs_mlp *mlp, void *stream);
+/* Standardised feature rows [num_batch, ceil(3n/32)*32] (BF16) and, when
+ * x_next is given, standardised targets [num_batch, n] (FP32), DEVICE. */
+bbs_status bbs_mlp_make_samples(bbs_mlp *mlp, const bbs_batch_matrix *A, const double *b,
+                                const double *x_prev, const double *x_next, uint16_t *feats,
+                                float *targets, void *stream);
+/* Loss and parameter gradients of the minibatch made of rows `rows` (DEVICE
+ * int32 [M]) of the sample store (feats, targets); M a multiple of 32 up to
+ * max_batch. *loss (DEVICE) receives the mean squared error; the gradients
+ * stay in the network (flat layout, see bbs_mlp_get_grads). */
+bbs_status bbs_mlp_gradients(bbs_mlp *mlp, const uint16_t *feats, const float *targets,
+                             const int32_t *rows, int32_t M, float *loss, void *stream);
+/* bbs_mlp_gradients followed by one Adam step with learning rate lr. */
+bbs_status bbs_mlp_train_step(bbs_mlp *mlp, const uint16_t *feats, const float *targets,
+                              const int32_t *rows, int32_t M, float lr, float *loss, void *stream);
+/* Copy the gradients (flat layout) of the last bbs_mlp_gradients /
+ * bbs_mlp_train_step to a DEVICE array. Asynchronous on stream. */
+bbs_status bbs_mlp_get_grads(bbs_mlp *mlp, float *grads, void *stream);
+/* Network output (standardised change) for M feature rows: out [M, n] FP32. */
+bbs_status bbs_mlp_forward(bbs_mlp *mlp, const uint16_t *feats, int32_t M, float *out, void *stream);
+/* Initial guesses for a whole batch: x0 = x_prev + predicted change (DEVICE
+ * FP64 [num_batch * n]). */
+bbs_status bbs_mlp_predict(bbs_mlp *mlp, const bbs_batch_matrix *A, const double *b,
+                           const double *x_prev, double *x0, void *stream);
+
 /* Threads per system by the rule of Sec. 3.6: at least n, a multiple of the
  * warp size 32, at most `max_threads` (the device maximum, 1024 on GB300).
  * Returns 0 for n <= 0 or max_threads < 32. Host only. */
 int32_t bbs_paper_block_size(int32_t n, int32_t max_threads);
 
-/* Threads per system the library uses by default for an n-row system: the
- * fewest warps that keep at most `rows_per_thread` rows per thread (which
- * keeps the working vectors in registers). Host only. */
+/* Threads per system for an n-row system at up to `rows_per_thread` rows per
+ * thread: the fewest warps that keep at most that many rows per thread (which
+ * keeps the working vectors in registers). The library uses 8 for the FP64
+ * solvers (fewest FP64 instructions per system) and 4 for the mixed mode.
+ * Host only. */
 int32_t bbs_default_block_size(int32_t n, int32_t rows_per_thread);
 
 /* Message of the last failed call on this host thread ("" if none). */

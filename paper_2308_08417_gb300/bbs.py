@@ -44,6 +44,40 @@ class bbs_log(C.Structure):
                 ("inner_iters", C.c_void_p)]
 
 
+class bbs_var_batch(C.Structure):
+    _fields_ = [("num_batch", C.c_int32), ("num_patterns", C.c_int32), ("pat_n", C.c_void_p),
+                ("pat_nnz", C.c_void_p), ("pat_rp_off", C.c_void_p), ("pat_ci_off", C.c_void_p),
+                ("row_ptrs", C.c_void_p), ("col_idxs", C.c_void_p), ("sys_pattern", C.c_void_p),
+                ("val_off", C.c_void_p), ("vec_off", C.c_void_p), ("values", C.c_void_p)]
+
+
+class bbs_var_host_info(C.Structure):
+    _fields_ = [("pat_n", C.c_void_p), ("pat_nnz", C.c_void_p), ("sys_pattern", C.c_void_p)]
+
+
+class bbs_var_tuning(C.Structure):
+    _fields_ = [("num_buckets", C.c_int32), ("bucket_max_n", C.c_int32 * 8),
+                ("team_warps", C.c_int32 * 8), ("stage_values", C.c_int32 * 8),
+                ("block_warps", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        k = self.num_buckets
+        return {"bucket_max_n": list(self.bucket_max_n[:k]), "team_warps": list(self.team_warps[:k]),
+                "stage_values": list(self.stage_values[:k]), "block_warps": self.block_warps}
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "bbs_var_tuning":
+        t = cls()
+        k = len(d["bucket_max_n"])
+        t.num_buckets = k
+        for i in range(k):
+            t.bucket_max_n[i] = d["bucket_max_n"][i]
+            t.team_warps[i] = d["team_warps"][i]
+            t.stage_values[i] = d["stage_values"][i]
+        t.block_warps = d["block_warps"]
+        return t
+
+
 _lib = None
 
 
@@ -67,6 +101,27 @@ def lib():
                                      P(bbs_options), P(bbs_log)]
         L.bbs_solve_noalloc.argtypes = [C.c_void_p, P(bbs_batch_matrix), C.c_void_p, C.c_void_p,
                                         P(bbs_options), P(bbs_log), C.c_void_p]
+        L.bbs_var_default_tuning.argtypes = [C.c_int32, P(bbs_var_tuning)]
+        L.bbs_var_plan_create.argtypes = [C.c_void_p, P(bbs_var_batch), P(bbs_var_host_info),
+                                          P(bbs_options), P(bbs_var_tuning), P(C.c_void_p)]
+        L.bbs_var_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, P(bbs_log), C.c_void_p]
+        L.bbs_var_plan_destroy.argtypes = [C.c_void_p]
+        L.bbs_var_tune.argtypes = [C.c_void_p, P(bbs_var_batch), P(bbs_var_host_info), C.c_void_p,
+                                   C.c_void_p, P(bbs_options), C.c_int32, P(bbs_var_tuning)]
+        vp, i32, st = C.c_void_p, C.c_int32, C.c_void_p
+        L.bbs_mlp_create.argtypes = [vp, i32, i32, C.c_uint64, i32, P(C.c_void_p)]
+        L.bbs_mlp_destroy.argtypes = [vp]
+        L.bbs_mlp_param_count.argtypes = [vp, P(C.c_int64)]
+        L.bbs_mlp_get_params.argtypes = [vp, vp, st]
+        L.bbs_mlp_set_params.argtypes = [vp, vp, st]
+        L.bbs_mlp_get_grads.argtypes = [vp, vp, st]
+        L.bbs_mlp_observe.argtypes = [vp, P(bbs_batch_matrix), vp, vp, vp, st]
+        L.bbs_mlp_finalize_stats.argtypes = [vp, st]
+        L.bbs_mlp_make_samples.argtypes = [vp, P(bbs_batch_matrix), vp, vp, vp, vp, vp, st]
+        L.bbs_mlp_gradients.argtypes = [vp, vp, vp, vp, i32, vp, st]
+        L.bbs_mlp_train_step.argtypes = [vp, vp, vp, vp, i32, C.c_float, vp, st]
+        L.bbs_mlp_forward.argtypes = [vp, vp, i32, vp, st]
+        L.bbs_mlp_predict.argtypes = [vp, P(bbs_batch_matrix), vp, vp, vp, st]
         L.bbs_paper_block_size.argtypes = [C.c_int32, C.c_int32]
         L.bbs_paper_block_size.restype = C.c_int32
         L.bbs_default_block_size.argtypes = [C.c_int32, C.c_int32]
@@ -74,7 +129,12 @@ def lib():
         L.bbs_last_error.restype = C.c_char_p
         L.bbs_version.restype = C.c_char_p
         for name in ("bbs_default_options", "bbs_create", "bbs_destroy", "bbs_workspace_size",
-                     "bbs_solve", "bbs_solve_host", "bbs_solve_noalloc"):
+                     "bbs_solve", "bbs_solve_host", "bbs_solve_noalloc", "bbs_var_default_tuning",
+                     "bbs_var_plan_create", "bbs_var_solve", "bbs_var_plan_destroy", "bbs_var_tune",
+                     "bbs_mlp_create", "bbs_mlp_destroy", "bbs_mlp_param_count", "bbs_mlp_get_params",
+                     "bbs_mlp_set_params", "bbs_mlp_get_grads", "bbs_mlp_observe",
+                     "bbs_mlp_finalize_stats", "bbs_mlp_make_samples", "bbs_mlp_gradients",
+                     "bbs_mlp_train_step", "bbs_mlp_forward", "bbs_mlp_predict"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -258,3 +318,189 @@ def solve(A: DeviceBatch, b: torch.Tensor, x0: torch.Tensor | None = None, handl
     ws = h.workspace(A, o)
     h.solve(A, b.contiguous(), x, o, log, ws)
     return x, log
+
+
+# ------------------------------------------------------------ uneven batches
+
+@dataclass
+class VarDeviceBatch:
+    """An uneven batch (workloads.VarBatch) on the device, plus the host metadata
+    the planner reads."""
+
+    tensors: dict
+    host: dict
+    num_batch: int
+    num_patterns: int
+    vec_len: int
+
+    @classmethod
+    def from_varbatch(cls, vb, device="cuda"):
+        import numpy as np
+
+        pat_n, pat_nnz, rp_off, ci_off, rps, cis = vb.pools()
+        t = {
+            "pat_n": torch.as_tensor(pat_n, dtype=torch.int32, device=device),
+            "pat_nnz": torch.as_tensor(pat_nnz, dtype=torch.int32, device=device),
+            "pat_rp_off": torch.as_tensor(rp_off, dtype=torch.int64, device=device),
+            "pat_ci_off": torch.as_tensor(ci_off, dtype=torch.int64, device=device),
+            "row_ptrs": torch.as_tensor(rps, dtype=torch.int32, device=device),
+            "col_idxs": torch.as_tensor(cis, dtype=torch.int32, device=device),
+            "sys_pattern": torch.as_tensor(vb.sys_pattern, dtype=torch.int32, device=device),
+            "val_off": torch.as_tensor(vb.val_off, dtype=torch.int64, device=device),
+            "vec_off": torch.as_tensor(vb.vec_off, dtype=torch.int64, device=device),
+            "values": torch.as_tensor(vb.values, dtype=torch.float64, device=device),
+        }
+        host = {"pat_n": np.ascontiguousarray(pat_n, dtype=np.int32),
+                "pat_nnz": np.ascontiguousarray(pat_nnz, dtype=np.int32),
+                "sys_pattern": np.ascontiguousarray(vb.sys_pattern, dtype=np.int32)}
+        return cls(t, host, vb.num_batch, len(vb.patterns), int(vb.b.shape[0]))
+
+    def struct(self) -> bbs_var_batch:
+        t = self.tensors
+        return bbs_var_batch(self.num_batch, self.num_patterns, *[_ptr(t[k]) for k in (
+            "pat_n", "pat_nnz", "pat_rp_off", "pat_ci_off", "row_ptrs", "col_idxs", "sys_pattern",
+            "val_off", "vec_off", "values")])
+
+    def host_struct(self) -> bbs_var_host_info:
+        h = self.host
+        return bbs_var_host_info(*[C.c_void_p(h[k].ctypes.data) for k in ("pat_n", "pat_nnz", "sys_pattern")])
+
+
+def bbs_var_default_tuning(max_n: int) -> bbs_var_tuning:
+    t = bbs_var_tuning()
+    _check(lib().bbs_var_default_tuning(int(max_n), C.byref(t)), "bbs_var_default_tuning")
+    return t
+
+
+def bbs_var_tune(handle: Handle, vbd: VarDeviceBatch, b: torch.Tensor, x0: torch.Tensor,
+                 opts: bbs_options, sample: int = 512) -> bbs_var_tuning:
+    t = bbs_var_tuning()
+    s, hs = vbd.struct(), vbd.host_struct()
+    _check(lib().bbs_var_tune(handle._h, C.byref(s), C.byref(hs), _ptr(b), _ptr(x0), C.byref(opts),
+                              int(sample), C.byref(t)), "bbs_var_tune")
+    return t
+
+
+class VarPlan:
+    """bbs_var_plan: a planned, graph-captured persistent solve of an uneven batch."""
+
+    def __init__(self, handle: Handle, vbd: VarDeviceBatch, opts: bbs_options,
+                 tuning: bbs_var_tuning | None = None):
+        p = C.c_void_p()
+        s, hs = vbd.struct(), vbd.host_struct()
+        _check(lib().bbs_var_plan_create(handle._h, C.byref(s), C.byref(hs), C.byref(opts),
+                                         None if tuning is None else C.byref(tuning), C.byref(p)),
+               "bbs_var_plan_create")
+        self._p = p
+        self._keep = (handle, vbd)
+
+    def solve(self, b: torch.Tensor, x: torch.Tensor, log: Log, stream=None):
+        lg = log.struct()
+        st = stream if stream is not None else torch.cuda.current_stream(b.device)
+        _check(lib().bbs_var_solve(self._p, _ptr(b), _ptr(x), C.byref(lg), C.c_void_p(st.cuda_stream)),
+               "bbs_var_solve")
+
+    def close(self):
+        if self._p:
+            lib().bbs_var_plan_destroy(self._p)
+            self._p = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------- learned guess
+
+def _stream(t):
+    return C.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+class MLP:
+    """bbs_mlp: the initial-guess network (weights, statistics, activations on
+    the device; every step runs in the library's kernels)."""
+
+    def __init__(self, handle: Handle, n: int, hidden: int = 256, seed: int = 0, max_batch: int = 4096):
+        p = C.c_void_p()
+        _check(lib().bbs_mlp_create(handle._h, int(n), int(hidden), int(seed), int(max_batch), C.byref(p)),
+               "bbs_mlp_create")
+        self._p = p
+        self._handle = handle
+        self.n, self.hidden, self.max_batch = int(n), int(hidden), int(max_batch)
+        self.in_pad = (3 * self.n + 31) // 32 * 32
+        cnt = C.c_int64()
+        _check(lib().bbs_mlp_param_count(p, C.byref(cnt)), "bbs_mlp_param_count")
+        self.param_count = int(cnt.value)
+        self.device = torch.device("cuda", handle.device)
+
+    def close(self):
+        if self._p:
+            lib().bbs_mlp_destroy(self._p)
+            self._p = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> torch.Tensor:
+        out = torch.empty(self.param_count, dtype=torch.float32, device=self.device)
+        _check(lib().bbs_mlp_get_params(self._p, _ptr(out), _stream(out)), "bbs_mlp_get_params")
+        return out
+
+    def set_params(self, params: torch.Tensor):
+        params = params.to(self.device, torch.float32).contiguous()
+        _check(lib().bbs_mlp_set_params(self._p, _ptr(params), _stream(params)), "bbs_mlp_set_params")
+
+    def get_grads(self) -> torch.Tensor:
+        out = torch.empty(self.param_count, dtype=torch.float32, device=self.device)
+        _check(lib().bbs_mlp_get_grads(self._p, _ptr(out), _stream(out)), "bbs_mlp_get_grads")
+        return out
+
+    def observe(self, A: DeviceBatch, b, x_prev, x_next):
+        s = A.struct()
+        _check(lib().bbs_mlp_observe(self._p, C.byref(s), _ptr(b), _ptr(x_prev), _ptr(x_next), _stream(b)),
+               "bbs_mlp_observe")
+
+    def finalize_stats(self):
+        _check(lib().bbs_mlp_finalize_stats(self._p, C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)),
+               "bbs_mlp_finalize_stats")
+
+    def make_samples(self, A: DeviceBatch, b, x_prev, x_next=None, feats=None, targets=None):
+        B = A.num_batch
+        if feats is None:
+            feats = torch.empty(B, self.in_pad, dtype=torch.bfloat16, device=self.device)
+        if x_next is not None and targets is None:
+            targets = torch.empty(B, self.n, dtype=torch.float32, device=self.device)
+        s = A.struct()
+        _check(lib().bbs_mlp_make_samples(self._p, C.byref(s), _ptr(b), _ptr(x_prev), _ptr(x_next),
+                                          _ptr(feats), _ptr(targets), _stream(b)), "bbs_mlp_make_samples")
+        return feats, targets
+
+    def gradients(self, feats, targets, rows, loss=None):
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device) if loss is None else loss
+        _check(lib().bbs_mlp_gradients(self._p, _ptr(feats), _ptr(targets), _ptr(rows), int(rows.numel()),
+                                       _ptr(loss), _stream(feats)), "bbs_mlp_gradients")
+        return loss
+
+    def train_step(self, feats, targets, rows, lr, loss=None):
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device) if loss is None else loss
+        _check(lib().bbs_mlp_train_step(self._p, _ptr(feats), _ptr(targets), _ptr(rows), int(rows.numel()),
+                                        float(lr), _ptr(loss), _stream(feats)), "bbs_mlp_train_step")
+        return loss
+
+    def forward(self, feats) -> torch.Tensor:
+        M = int(feats.shape[0])
+        out = torch.empty(M, self.n, dtype=torch.float32, device=self.device)
+        _check(lib().bbs_mlp_forward(self._p, _ptr(feats), M, _ptr(out), _stream(feats)), "bbs_mlp_forward")
+        return out
+
+    def predict(self, A: DeviceBatch, b, x_prev, x0=None):
+        x0 = torch.empty_like(x_prev) if x0 is None else x0
+        s = A.struct()
+        _check(lib().bbs_mlp_predict(self._p, C.byref(s), _ptr(b), _ptr(x_prev), _ptr(x0), _stream(b)),
+               "bbs_mlp_predict")
+        return x0

@@ -51,7 +51,14 @@ size_t vals_per_system(const bbs_batch_matrix* A) {
     }
 }
 
-constexpr int kDefaultRowsPerThread = 5;
+// Default rows per thread: FP64 arithmetic is the scarce resource, so the FP64
+// solvers use the fewest warps per system (up to 8 rows per thread); the mixed
+// mode's FP32 inner loop is latency-bound and prefers 4 rows per thread.
+constexpr int kDefaultRowsPerThread = 8;
+constexpr int kMixedRowsPerThread = 4;
+// Values are staged in shared memory by default when a block's shared memory
+// stays within this size (two blocks per SM).
+constexpr size_t kAutoStageBytes = 116 * 1024;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -109,8 +116,8 @@ int max_row_len(const bbs_batch_matrix* A) { return A->fmt == BBS_FMT_ELL ? A->e
 
 bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_options* o, Plan* p) {
     const int n = A->n;
-    p->threads = o->threads_per_system ? o->threads_per_system
-                                       : bbs_default_block_size(n, kDefaultRowsPerThread);
+    const int rpt = o->precision == BBS_PRECISION_MIXED_IR ? kMixedRowsPerThread : kDefaultRowsPerThread;
+    p->threads = o->threads_per_system ? o->threads_per_system : bbs_default_block_size(n, rpt);
     if (p->threads <= 0)
         return fail(BBS_ERR_UNSUPPORTED, "n = %d exceeds the largest supported system (%d rows)", n,
                     bbs::kMaxRows);
@@ -146,7 +153,7 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
     if (o->values_in_smem == 1)
         stage = base + stage_bytes <= limit;
     else if (o->values_in_smem == 0)
-        stage = base + stage_bytes <= 64 * 1024;
+        stage = base + stage_bytes <= kAutoStageBytes;
     if (base > limit) return fail(BBS_ERR_UNSUPPORTED, "shared memory need %zu exceeds %zu", base, limit);
     p->stage = stage;
     p->stage_off = base;

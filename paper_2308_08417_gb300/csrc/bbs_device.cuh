@@ -34,23 +34,40 @@ struct Mat {
     int k;  // ELL width
 };
 
+// A team of whole warps that solves one system: the whole block (bar == 0,
+// synchronised with __syncthreads), a single warp (__syncwarp), or a group of
+// warps inside a persistent block (named barrier `bar`, 1..15).
 struct Team {
-    int tid, nt, lane, warp, nwarps;
-    __device__ __forceinline__ static Team make() {
+    int tid, nt, lane, warp, nwarps, bar;
+    __device__ __forceinline__ static Team block() {
         Team t;
         t.tid = threadIdx.x;
         t.nt = blockDim.x;
         t.lane = threadIdx.x & 31;
         t.warp = threadIdx.x >> 5;
         t.nwarps = blockDim.x >> 5;
+        t.bar = 0;
+        return t;
+    }
+    // Warps [first_warp, first_warp + nwarps) of the block.
+    __device__ __forceinline__ static Team group(int first_warp, int nwarps) {
+        Team t;
+        t.tid = threadIdx.x - first_warp * 32;
+        t.nt = nwarps * 32;
+        t.lane = threadIdx.x & 31;
+        t.warp = (threadIdx.x >> 5) - first_warp;
+        t.nwarps = nwarps;
+        t.bar = (nwarps * 32 == (int)blockDim.x) ? 0 : 1 + first_warp;
         return t;
     }
     __device__ __forceinline__ int row(int q) const { return tid + q * nt; }
     __device__ __forceinline__ void sync() const {
         if (nwarps == 1)
             __syncwarp();
-        else
+        else if (bar == 0)
             __syncthreads();
+        else
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
     }
 };
 
@@ -59,6 +76,17 @@ __device__ __forceinline__ V ldg(const V* p) { return __ldg(p); }
 
 template <typename T>
 __device__ __forceinline__ bool finite(T v) { return isfinite(v); }
+
+// FP64 tests done on the integer pipe (the FP64 pipe is the scarce resource
+// of the FP64 solvers): finiteness, exact zero, and a <= b for a, b >= +0
+// (the bit patterns of non-negative doubles order like the values).
+__device__ __forceinline__ bool finite64(double v) {
+    return (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool zero64(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ bool le_nonneg64(double a, double b) {
+    return __double_as_longlong(a) <= __double_as_longlong(b);
+}
 
 // a_ii of row `row` (0 when the pattern stores none).
 template <int FMT, typename V>
@@ -96,7 +124,9 @@ __device__ __forceinline__ void jacobi_setup(const Mat<V>& A, bool jacobi, T (&d
 }
 
 // y = A x for the caller's rows; x is a shared-memory vector of length n.
-// Entries are accumulated in stored (ascending column) order with FMA.
+// Entries are accumulated in stored (ascending column) order with FMA. The
+// CSR loop runs the warp's longest row with a predicate, so the warp never
+// diverges on row lengths.
 template <int FMT, int R, typename T, typename V>
 __device__ __forceinline__ void spmv(const Mat<V>& A, const T* __restrict__ xs, T (&y)[R],
                                      const Team& tm) {
@@ -104,7 +134,14 @@ __device__ __forceinline__ void spmv(const Mat<V>& A, const T* __restrict__ xs, 
     for (int q = 0; q < R; ++q) {
         const int row = tm.row(q);
         T sum = T(0);
-        if (row < A.n) {
+        if constexpr (FMT == FMT_CSR) {
+            const bool ok = row < A.n;
+            const int e0 = ok ? ldg(A.row_ptrs + row) : 0;
+            const int len = ok ? ldg(A.row_ptrs + row + 1) - e0 : 0;
+            const int longest = __reduce_max_sync(kFull, len);
+            for (int j = 0; j < longest; ++j)
+                if (j < len) sum = fma(T(ldg(A.vals + e0 + j)), xs[ldg(A.cols + e0 + j)], sum);
+        } else if (row < A.n) {
             if constexpr (FMT == FMT_ELL) {
                 const int32_t* c = A.cols + row;
                 const V* a = A.vals + row;
@@ -112,9 +149,6 @@ __device__ __forceinline__ void spmv(const Mat<V>& A, const T* __restrict__ xs, 
                     const int col = ldg(c + (size_t)j * A.n);
                     if (col >= 0) sum = fma(T(ldg(a + (size_t)j * A.n)), xs[col], sum);
                 }
-            } else if constexpr (FMT == FMT_CSR) {
-                const int e0 = ldg(A.row_ptrs + row), e1 = ldg(A.row_ptrs + row + 1);
-                for (int e = e0; e < e1; ++e) sum = fma(T(ldg(A.vals + e)), xs[ldg(A.cols + e)], sum);
             } else {
                 const V* a = A.vals + (size_t)row * A.n;
                 for (int j = 0; j < A.n; ++j) sum = fma(T(ldg(a + j)), xs[j], sum);
@@ -133,15 +167,19 @@ __device__ __forceinline__ void spmv_staged(const Mat<V>& A, const V* __restrict
     for (int q = 0; q < R; ++q) {
         const int row = tm.row(q);
         T sum = T(0);
-        if (row < A.n) {
+        if constexpr (FMT == FMT_CSR) {
+            const bool ok = row < A.n;
+            const int e0 = ok ? ldg(A.row_ptrs + row) : 0;
+            const int len = ok ? ldg(A.row_ptrs + row + 1) - e0 : 0;
+            const int longest = __reduce_max_sync(kFull, len);
+            for (int j = 0; j < longest; ++j)
+                if (j < len) sum = fma(T(as[e0 + j]), xs[ldg(A.cols + e0 + j)], sum);
+        } else if (row < A.n) {
             if constexpr (FMT == FMT_ELL) {
                 for (int j = 0; j < A.k; ++j) {
                     const int col = ldg(A.cols + (size_t)j * A.n + row);
                     if (col >= 0) sum = fma(T(as[(size_t)j * A.n + row]), xs[col], sum);
                 }
-            } else if constexpr (FMT == FMT_CSR) {
-                const int e0 = ldg(A.row_ptrs + row), e1 = ldg(A.row_ptrs + row + 1);
-                for (int e = e0; e < e1; ++e) sum = fma(T(as[e]), xs[ldg(A.cols + e)], sum);
             } else {
                 const V* a = as + (size_t)row * A.n;
                 for (int j = 0; j < A.n; ++j) sum = fma(T(a[j]), xs[j], sum);
@@ -234,7 +272,7 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* red, int& parity, const
 #pragma unroll
         for (int j = 0; j < NV; ++j) buf[tm.warp * 4 + j] = v[j];
     }
-    __syncthreads();
+    tm.sync();
     if (tm.nwarps <= 4) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) {

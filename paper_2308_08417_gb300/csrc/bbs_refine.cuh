@@ -93,9 +93,10 @@ __device__ __forceinline__ int inner_bicgstab32(const Op<FMT, R, float, float>& 
 template <int FMT, int R>
 __global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const SolveParams P) {
     extern __shared__ __align__(16) unsigned char raw[];
-    const Team tm = Team::make();
+    const Team tm = Team::block();
     const int sys = blockIdx.x;
     const int n = P.n;
+    const SysIO io = sys_io(P, sys);
     double* red64 = reinterpret_cast<double*>(raw);
     double* xd = red64 + 256;
     float* red32 = reinterpret_cast<float*>(xd + P.n_pad);
@@ -110,27 +111,27 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const Sol
     if (P.stage) {
         float* s = reinterpret_cast<float*>(raw + P.stage_off);
         stage_values(A32.vals, s, P.vps, tm);
-        __syncthreads();
+        tm.sync();
         as = s;
     }
     const Op<FMT, R, float, float> op32{A32, as};
 
     double b[R], x[R], r[R];
     float dinv[R], w[R], d[R];
-    load_system<FMT, R>(P, sys, b, x, tm);
+    load_system<R>(io, b, x, tm);
     jacobi_setup<FMT, R>(A32, P.precond == 1, dinv, tm);
 
     double s0[1] = {pdot(b, b)};
     block_sum(s0, red64, par64, tm);
     const double nb2 = s0[0];
     if (!finite(nb2)) {
-        write_result(P, sys, x, ST_NAN, 0, __longlong_as_double(0x7ff8000000000000LL), 0, tm);
+        write_result(io, x, ST_NAN, 0, quiet_nan(), 0, tm);
         return;
     }
     if (nb2 == 0.0) {
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = 0.0;
-        write_result(P, sys, x, ST_CONVERGED, 0, 0.0, 0, tm);
+        write_result(io, x, ST_CONVERGED, 0, 0.0, 0, tm);
         return;
     }
     const double tau2 = (P.tol_type == 1) ? P.tol * P.tol * nb2 : P.tol * P.tol;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const Sol
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = fma(rn, (double)d[q], x[q]);
     }
-    write_result(P, sys, x, status, k, sqrt(rr / nb2), inner_total, tm);
+    write_result(io, x, status, k, sqrt(rr / nb2), inner_total, tm);
 }
 
 // FP32 copy of the values for the mixed mode (when the caller gives none).

@@ -32,17 +32,16 @@ struct Op {
     }
 };
 
-// Shared-memory layout common to the FP64 solvers:
-//   red [256] | xa [n_pad] | xb [n_pad] | extra solver space | staged values
-struct Smem64 {
+// Shared memory of one team: red [256] | xa [n_pad] | xb [n_pad] | extra
+struct TeamSmem {
     double* red;
     double* xa;
     double* xb;
     double* extra;
 };
 
-__device__ __forceinline__ Smem64 smem64_layout(unsigned char* raw, int n_pad) {
-    Smem64 s;
+__device__ __forceinline__ TeamSmem team_smem(unsigned char* raw, int n_pad) {
+    TeamSmem s;
     s.red = reinterpret_cast<double*>(raw);
     s.xa = s.red + 256;
     s.xb = s.xa + n_pad;
@@ -50,7 +49,49 @@ __device__ __forceinline__ Smem64 smem64_layout(unsigned char* raw, int n_pad) {
     return s;
 }
 
-// Residual r = b - A x (x staged through xs) and ||r||^2 for the log.
+// One system's vectors and log entries.
+struct SysIO {
+    const double* b;
+    double* x;
+    int32_t* iters;
+    double* rel_res;
+    int32_t* status;
+    int32_t* inner;  // may be null
+    int n;
+};
+
+struct SolveCfg {
+    int precond, tol_type, max_iters, restart, max_outer;
+    double tol, inner_tol;
+    double* ws;  // this system's workspace slice (GMRES basis) or null
+};
+
+__device__ __forceinline__ SysIO sys_io(const SolveParams& P, int sys) {
+    SysIO io;
+    io.b = P.b + (size_t)sys * P.n;
+    io.x = P.x + (size_t)sys * P.n;
+    io.iters = P.iters + sys;
+    io.rel_res = P.rel_res + sys;
+    io.status = P.status + sys;
+    io.inner = P.inner_iters != nullptr ? P.inner_iters + sys : nullptr;
+    io.n = P.n;
+    return io;
+}
+
+__device__ __forceinline__ SolveCfg solve_cfg(const SolveParams& P, int sys) {
+    SolveCfg c;
+    c.precond = P.precond;
+    c.tol_type = P.tol_type;
+    c.max_iters = P.max_iters;
+    c.restart = P.restart;
+    c.max_outer = P.max_outer;
+    c.tol = P.tol;
+    c.inner_tol = P.inner_tol;
+    c.ws = P.ws != nullptr ? P.ws + (size_t)sys * (P.restart + 1) * P.n_pad : nullptr;
+    return c;
+}
+
+// Residual r = b - A x (x staged through xs) and ||r||^2.
 template <int FMT, int R, typename V>
 __device__ __forceinline__ double true_residual(const Op<FMT, R, double, V>& op,
                                                 const double (&b)[R], const double (&x)[R],
@@ -68,51 +109,51 @@ __device__ __forceinline__ double true_residual(const Op<FMT, R, double, V>& op,
 }
 
 template <int R>
-__device__ __forceinline__ void write_result(const SolveParams& P, int sys, const double (&x)[R],
-                                             int status, int iters, double rel, int inner,
-                                             const Team& tm) {
-    double* xg = P.x + (size_t)sys * P.n;
+__device__ __forceinline__ void write_result(const SysIO& io, const double (&x)[R], int status,
+                                             int iters, double rel, int inner, const Team& tm) {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int row = tm.row(q);
-        if (row < P.n) xg[row] = x[q];
+        if (row < io.n) io.x[row] = x[q];
     }
     if (tm.tid == 0) {
-        P.iters[sys] = iters;
-        P.rel_res[sys] = rel;
-        P.status[sys] = status;
-        if (P.inner_iters != nullptr) P.inner_iters[sys] = inner;
+        *io.iters = iters;
+        *io.rel_res = rel;
+        *io.status = status;
+        if (io.inner != nullptr) *io.inner = inner;
     }
 }
 
-template <int FMT, int R>
-__device__ __forceinline__ void load_system(const SolveParams& P, int sys, double (&b)[R],
-                                            double (&x)[R], const Team& tm) {
-    const double* bg = P.b + (size_t)sys * P.n;
-    const double* xg = P.x + (size_t)sys * P.n;
+template <int R>
+__device__ __forceinline__ void load_system(const SysIO& io, double (&b)[R], double (&x)[R],
+                                            const Team& tm) {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int row = tm.row(q);
-        b[q] = (row < P.n) ? bg[row] : 0.0;
-        x[q] = (row < P.n) ? xg[row] : 0.0;
+        b[q] = (row < io.n) ? io.b[row] : 0.0;
+        x[q] = (row < io.n) ? io.x[row] : 0.0;
     }
 }
 
-// Prologue shared by the solvers: staging, b, x0, Jacobi, r0 = b - A x0 and
-// (||b||^2, ||r0||^2). Returns the Op for this system.
+__device__ __forceinline__ double quiet_nan() { return quiet_nan(); }
+
+// The system's values, staged in shared memory at `stage` when non-null.
+template <int FMT, int R>
+__device__ __forceinline__ Op<FMT, R, double, double> make_op(const Mat<double>& A, size_t vps,
+                                                              double* stage, const Team& tm) {
+    if (stage != nullptr) {
+        stage_values(A.vals, stage, vps, tm);
+        tm.sync();
+    }
+    return Op<FMT, R, double, double>{A, stage};
+}
+
 template <int FMT, int R>
 __device__ __forceinline__ Op<FMT, R, double, double> make_op(const SolveParams& P, int sys,
-                                                              unsigned char* raw, size_t stage_off,
-                                                              const Team& tm) {
-    Mat<double> A{P.values + (size_t)sys * P.vps, P.row_ptrs, P.cols, P.n, P.k};
-    const double* as = nullptr;
-    if (P.stage) {
-        double* s = reinterpret_cast<double*>(raw + stage_off);
-        stage_values(A.vals, s, P.vps, tm);
-        __syncthreads();
-        as = s;
-    }
-    return Op<FMT, R, double, double>{A, as};
+                                                              unsigned char* raw, const Team& tm) {
+    const Mat<double> A{P.values + (size_t)sys * P.vps, P.row_ptrs, P.cols, P.n, P.k};
+    double* stage = P.stage ? reinterpret_cast<double*>(raw + P.stage_off) : nullptr;
+    return make_op<FMT, R>(A, P.vps, stage, tm);
 }
 
 // ------------------------------------------------------------- BiCGSTAB
@@ -127,18 +168,13 @@ __device__ __forceinline__ Op<FMT, R, double, double> make_op(const SolveParams&
 // s-test shares a reduction with omega (the t of an exiting iteration is
 // simply unused).
 template <int FMT, int R>
-__global__ void __launch_bounds__(max_threads_for(R), 1) bicgstab_kernel(const SolveParams P) {
-    extern __shared__ __align__(16) unsigned char raw[];
-    const Team tm = Team::make();
-    const int sys = blockIdx.x;
-    const int n = P.n;
-    const Smem64 sm = smem64_layout(raw, P.n_pad);
-    const auto op = make_op<FMT, R>(P, sys, raw, P.stage_off, tm);
+__device__ __forceinline__ void bicgstab_system(const Op<FMT, R, double, double>& op, const SysIO& io,
+                                          const SolveCfg& C, const TeamSmem& sm, const Team& tm) {
+    const int n = io.n;
     int parity = 0;
-
     double b[R], x[R], r[R], rh[R], p[R], v[R], dinv[R], t[R];
-    load_system<FMT, R>(P, sys, b, x, tm);
-    jacobi_setup<FMT, R>(op.A, P.precond == 1, dinv, tm);
+    load_system<R>(io, b, x, tm);
+    jacobi_setup<FMT, R>(op.A, C.precond == 1, dinv, tm);
 
     put(sm.xa, x, tm, n);
     tm.sync();
@@ -154,16 +190,16 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) bicgstab_kernel(const S
     double res2 = rr;  // squared true residual of x (valid when have_res)
     bool have_res = true;
     if (!finite(nb2)) {
-        write_result(P, sys, x, ST_NAN, 0, __longlong_as_double(0x7ff8000000000000LL), 0, tm);
+        write_result(io, x, ST_NAN, 0, quiet_nan(), 0, tm);
         return;
     }
     if (nb2 == 0.0) {
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = 0.0;
-        write_result(P, sys, x, ST_CONVERGED, 0, 0.0, 0, tm);
+        write_result(io, x, ST_CONVERGED, 0, 0.0, 0, tm);
         return;
     }
-    const double tau2 = (P.tol_type == 1) ? P.tol * P.tol * nb2 : P.tol * P.tol;
+    const double tau2 = (C.tol_type == 1) ? C.tol * C.tol * nb2 : C.tol * C.tol;
     if (!finite(rr)) {
         status = ST_NAN;
     } else if (rr <= tau2) {
@@ -179,7 +215,7 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) bicgstab_kernel(const S
             v[q] = 0.0;
         }
         have_res = false;
-        for (int it = 1; it <= P.max_iters; ++it) {
+        for (int it = 1; it <= C.max_iters; ++it) {
             iters = it;
             if (!finite(rho)) { status = ST_NAN; break; }
             if (rho == 0.0) { status = ST_BREAKDOWN; break; }
@@ -263,7 +299,181 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) bicgstab_kernel(const S
         if (status < 0) status = ST_MAX_ITER;
     }
     if (!have_res) res2 = true_residual(op, b, x, r, sm.xa, sm.red, parity, tm, n);
-    write_result(P, sys, x, status, iters, sqrt(res2 / nb2), 0, tm);
+    write_result(io, x, status, iters, sqrt(res2 / nb2), 0, tm);
+}
+
+// Scale the staged values in place by the Jacobi inverse diagonal of their
+// column, As = A D^-1 (each thread rescales the entries of its own rows; dinv
+// is shared through `tmp` for the column lookups).
+template <int FMT, int R>
+__device__ __forceinline__ void scale_columns(const Mat<double>& A, double* as, const double (&dinv)[R],
+                                              double* tmp, const Team& tm) {
+    put(tmp, dinv, tm, A.n);
+    tm.sync();
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        if (row >= A.n) continue;
+        if constexpr (FMT == FMT_CSR) {
+            const int e1 = ldg(A.row_ptrs + row + 1);
+            for (int e = ldg(A.row_ptrs + row); e < e1; ++e) as[e] *= tmp[ldg(A.cols + e)];
+        } else if constexpr (FMT == FMT_ELL) {
+            for (int j = 0; j < A.k; ++j) {
+                const int col = ldg(A.cols + (size_t)j * A.n + row);
+                if (col >= 0) as[(size_t)j * A.n + row] *= tmp[col];
+            }
+        } else {
+            for (int j = 0; j < A.n; ++j) as[(size_t)row * A.n + j] *= tmp[j];
+        }
+    }
+    tm.sync();
+}
+
+// BiCGSTAB with the Jacobi preconditioner folded into the staged matrix:
+// with As = A D^-1 and x~ = D x, right-preconditioned BiCGSTAB on A x = b is
+// plain BiCGSTAB on As x~ = b (p^ = D^-1 p and s^ = D^-1 s never need forming;
+// x~ += alpha p + omega s). Same iterates as bicgstab_system up to rounding,
+// two FP64 multiplies per row and iteration fewer. Scalar tests run on the
+// integer pipe. x = D^-1 x~ on exit.
+template <int FMT, int R>
+__device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, double>& op,
+                                                       const SysIO& io, const SolveCfg& C,
+                                                       const TeamSmem& sm, const Team& tm) {
+    const int n = io.n;
+    int parity = 0;
+    double b[R], x0[R], xs[R], r[R], rh[R], p[R], v[R], dinv[R], t[R];
+    load_system<R>(io, b, x0, tm);
+    jacobi_setup<FMT, R>(op.A, true, dinv, tm);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        const double d = row < n ? diag_entry<FMT>(op.A, row) : 0.0;
+        xs[q] = (d != 0.0) ? d * x0[q] : x0[q];  // x~ = D x (1 for a zero diagonal)
+    }
+    scale_columns<FMT, R>(op.A, const_cast<double*>(op.as), dinv, sm.xb, tm);
+
+    put(sm.xa, xs, tm, n);
+    tm.sync();
+    op.apply(sm.xa, t, tm);
+#pragma unroll
+    for (int q = 0; q < R; ++q) r[q] = b[q] - t[q];
+    double s0[2] = {pdot(b, b), pdot(r, r)};
+    block_sum(s0, sm.red, parity, tm);
+    const double nb2 = s0[0];
+    double rr = s0[1];
+    if (!finite64(nb2)) {
+        write_result(io, x0, ST_NAN, 0, quiet_nan(), 0, tm);
+        return;
+    }
+    if (zero64(nb2)) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) x0[q] = 0.0;
+        write_result(io, x0, ST_CONVERGED, 0, 0.0, 0, tm);
+        return;
+    }
+    int status = -1, iters = 0;
+    double res2 = rr;
+    bool have_res = true;
+    const double tau2 = (C.tol_type == 1) ? C.tol * C.tol * nb2 : C.tol * C.tol;
+    if (!finite64(rr)) {
+        status = ST_NAN;
+    } else if (le_nonneg64(rr, tau2)) {
+        status = ST_CONVERGED;
+    } else {
+        double rho = rr, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        int restarts = 0;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            rh[q] = r[q];
+            p[q] = 0.0;
+            v[q] = 0.0;
+        }
+        have_res = false;
+        for (int it = 1; it <= C.max_iters; ++it) {
+            iters = it;
+            if (!finite64(rho)) { status = ST_NAN; break; }
+            if (zero64(rho)) { status = ST_BREAKDOWN; break; }
+            const double beta = (rho * alpha) / (rho_old * omega);
+#pragma unroll
+            for (int q = 0; q < R; ++q) p[q] = fma(beta, fma(-omega, v[q], p[q]), r[q]);
+            put(sm.xa, p, tm, n);
+            tm.sync();
+            op.apply(sm.xa, v, tm);
+            double s1[1] = {pdot(rh, v)};
+            block_sum(s1, sm.red, parity, tm);
+            const double sigma = s1[0];
+            if (!finite64(sigma)) { status = ST_NAN; break; }
+            if (zero64(sigma)) { status = ST_BREAKDOWN; break; }
+            alpha = rho / sigma;
+#pragma unroll
+            for (int q = 0; q < R; ++q) r[q] = fma(-alpha, v[q], r[q]);  // r holds s
+            put(sm.xb, r, tm, n);
+            tm.sync();
+            op.apply(sm.xb, t, tm);
+            double s3[3] = {pdot(r, r), pdot(t, t), pdot(t, r)};
+            block_sum(s3, sm.red, parity, tm);
+            const double ss = s3[0], tt = s3[1], ts = s3[2];
+            if (!finite64(ss)) { status = ST_NAN; break; }
+            bool candidate;
+            double rho_next = 0.0;
+            if (le_nonneg64(ss, tau2)) {
+#pragma unroll
+                for (int q = 0; q < R; ++q) xs[q] = fma(alpha, p[q], xs[q]);
+                candidate = true;
+            } else {
+                if (!finite64(tt) || !finite64(ts)) { status = ST_NAN; break; }
+                omega = zero64(tt) ? 0.0 : ts / tt;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    xs[q] = fma(omega, r[q], fma(alpha, p[q], xs[q]));
+                    r[q] = fma(-omega, t[q], r[q]);
+                }
+                double s2[2] = {pdot(r, r), pdot(rh, r)};
+                block_sum(s2, sm.red, parity, tm);
+                rr = s2[0];
+                rho_next = s2[1];
+                if (!finite64(rr)) { status = ST_NAN; break; }
+                candidate = le_nonneg64(rr, tau2);
+            }
+            if (candidate) {
+                res2 = true_residual(op, b, xs, r, sm.xa, sm.red, parity, tm, n);
+                have_res = true;
+                if (!finite64(res2)) { status = ST_NAN; break; }
+                if (le_nonneg64(res2, tau2)) { status = ST_CONVERGED; break; }
+                if (++restarts > kMaxRestarts) { status = ST_MAX_ITER; break; }
+                have_res = false;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    rh[q] = r[q];
+                    p[q] = 0.0;
+                    v[q] = 0.0;
+                }
+                rho = res2;
+                rho_old = alpha = omega = 1.0;
+                continue;
+            }
+            if (zero64(omega)) { status = ST_BREAKDOWN; break; }
+            rho_old = rho;
+            rho = rho_next;
+        }
+        if (status < 0) status = ST_MAX_ITER;
+    }
+    if (!have_res) res2 = true_residual(op, b, xs, r, sm.xa, sm.red, parity, tm, n);
+    if (iters > 0) {  // with no iteration the guess is returned unchanged
+#pragma unroll
+        for (int q = 0; q < R; ++q) x0[q] = dinv[q] * xs[q];
+    }
+    write_result(io, x0, status, iters, sqrt(res2 / nb2), 0, tm);
+}
+
+// BiCGSTAB entry: the folded form when the values are staged and Jacobi is on.
+template <int FMT, int R>
+__device__ __forceinline__ void bicgstab_any(const Op<FMT, R, double, double>& op, const SysIO& io,
+                                             const SolveCfg& C, const TeamSmem& sm, const Team& tm) {
+    if (op.as != nullptr && C.precond == 1)
+        bicgstab_scaled_system<FMT, R>(op, io, C, sm, tm);
+    else
+        bicgstab_system<FMT, R>(op, io, C, sm, tm);
 }
 
 // ------------------------------------------------------------------- CG
@@ -272,18 +482,13 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) bicgstab_kernel(const S
 // x += alpha p ; r -= alpha t ; z = M r ; rho^ = r.z ; p = z + (rho^/rho) p.
 // Two reductions per iteration: (p.t) and (r.r, r.z).
 template <int FMT, int R>
-__global__ void __launch_bounds__(max_threads_for(R), 1) cg_kernel(const SolveParams P) {
-    extern __shared__ __align__(16) unsigned char raw[];
-    const Team tm = Team::make();
-    const int sys = blockIdx.x;
-    const int n = P.n;
-    const Smem64 sm = smem64_layout(raw, P.n_pad);
-    const auto op = make_op<FMT, R>(P, sys, raw, P.stage_off, tm);
+__device__ __forceinline__ void cg_system(const Op<FMT, R, double, double>& op, const SysIO& io,
+                                          const SolveCfg& C, const TeamSmem& sm, const Team& tm) {
+    const int n = io.n;
     int parity = 0;
-
     double b[R], x[R], r[R], z[R], p[R], t[R], dinv[R];
-    load_system<FMT, R>(P, sys, b, x, tm);
-    jacobi_setup<FMT, R>(op.A, P.precond == 1, dinv, tm);
+    load_system<R>(io, b, x, tm);
+    jacobi_setup<FMT, R>(op.A, C.precond == 1, dinv, tm);
 
     put(sm.xa, x, tm, n);
     tm.sync();
@@ -302,16 +507,16 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) cg_kernel(const SolvePa
     double res2 = rr;
     bool have_res = true;
     if (!finite(nb2)) {
-        write_result(P, sys, x, ST_NAN, 0, __longlong_as_double(0x7ff8000000000000LL), 0, tm);
+        write_result(io, x, ST_NAN, 0, quiet_nan(), 0, tm);
         return;
     }
     if (nb2 == 0.0) {
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = 0.0;
-        write_result(P, sys, x, ST_CONVERGED, 0, 0.0, 0, tm);
+        write_result(io, x, ST_CONVERGED, 0, 0.0, 0, tm);
         return;
     }
-    const double tau2 = (P.tol_type == 1) ? P.tol * P.tol * nb2 : P.tol * P.tol;
+    const double tau2 = (C.tol_type == 1) ? C.tol * C.tol * nb2 : C.tol * C.tol;
     if (!finite(rr)) {
         status = ST_NAN;
     } else if (rr <= tau2) {
@@ -321,7 +526,7 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) cg_kernel(const SolvePa
         int restarts = 0;
 #pragma unroll
         for (int q = 0; q < R; ++q) p[q] = z[q];
-        for (int it = 1; it <= P.max_iters; ++it) {
+        for (int it = 1; it <= C.max_iters; ++it) {
             iters = it;
             if (!finite(rho)) { status = ST_NAN; break; }
             if (rho == 0.0) { status = ST_BREAKDOWN; break; }
@@ -375,7 +580,7 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) cg_kernel(const SolvePa
         if (status < 0) status = ST_MAX_ITER;
     }
     if (!have_res) res2 = true_residual(op, b, x, r, sm.xa, sm.red, parity, tm, n);
-    write_result(P, sys, x, status, iters, sqrt(res2 / nb2), 0, tm);
+    write_result(io, x, status, iters, sqrt(res2 / nb2), 0, tm);
 }
 
 // ---------------------------------------------------------------- GMRES
@@ -387,14 +592,10 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) cg_kernel(const SolvePa
 // lives in shared memory or, when it does not fit, in the workspace; each
 // thread only touches its own rows of it.
 template <int FMT, int R>
-__global__ void __launch_bounds__(max_threads_for(R), 1) gmres_kernel(const SolveParams P) {
-    extern __shared__ __align__(16) unsigned char raw[];
-    const Team tm = Team::make();
-    const int sys = blockIdx.x;
-    const int n = P.n;
-    const int m = P.restart;
-    const Smem64 sm = smem64_layout(raw, P.n_pad);
-    const auto op = make_op<FMT, R>(P, sys, raw, P.stage_off, tm);
+__device__ __forceinline__ void gmres_system(const Op<FMT, R, double, double>& op, const SysIO& io,
+                                          const SolveCfg& C, const TeamSmem& sm, const Team& tm) {
+    const int n = io.n;
+    const int m = C.restart;
     int parity = 0;
     // extra: H[(m+1)*m] | cs[m] | sn[m] | g[m+1] | y[m] | ctl[4] | V (if in smem)
     double* H = sm.extra;
@@ -403,12 +604,12 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) gmres_kernel(const Solv
     double* g = sn + m;
     double* y = g + m + 1;
     int* ctl = reinterpret_cast<int*>(y + m);
-    double* V = (P.ws != nullptr) ? P.ws + (size_t)sys * (m + 1) * P.n_pad : y + m + 2;
-    const size_t vstride = P.n_pad;
+    double* V = (C.ws != nullptr) ? C.ws : y + m + 2;
+    const size_t vstride = (size_t)((n + 1) & ~1);
 
     double b[R], x[R], r[R], w[R], dinv[R];
-    load_system<FMT, R>(P, sys, b, x, tm);
-    jacobi_setup<FMT, R>(op.A, P.precond == 1, dinv, tm);
+    load_system<R>(io, b, x, tm);
+    jacobi_setup<FMT, R>(op.A, C.precond == 1, dinv, tm);
     put(sm.xa, x, tm, n);
     tm.sync();
     op.apply(sm.xa, w, tm);
@@ -419,16 +620,16 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) gmres_kernel(const Solv
     const double nb2 = s0[0];
     double beta2 = s0[1];
     if (!finite(nb2)) {
-        write_result(P, sys, x, ST_NAN, 0, __longlong_as_double(0x7ff8000000000000LL), 0, tm);
+        write_result(io, x, ST_NAN, 0, quiet_nan(), 0, tm);
         return;
     }
     if (nb2 == 0.0) {
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = 0.0;
-        write_result(P, sys, x, ST_CONVERGED, 0, 0.0, 0, tm);
+        write_result(io, x, ST_CONVERGED, 0, 0.0, 0, tm);
         return;
     }
-    const double tau2 = (P.tol_type == 1) ? P.tol * P.tol * nb2 : P.tol * P.tol;
+    const double tau2 = (C.tol_type == 1) ? C.tol * C.tol * nb2 : C.tol * C.tol;
     const double tau = sqrt(tau2);
     int status = -1, it = 0, restarts = 0;
     if (!finite(beta2))
@@ -436,7 +637,7 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) gmres_kernel(const Solv
     else if (beta2 <= tau2)
         status = ST_CONVERGED;
     while (status < 0) {
-        if (it >= P.max_iters) { status = ST_MAX_ITER; break; }
+        if (it >= C.max_iters) { status = ST_MAX_ITER; break; }
         const double beta = sqrt(beta2);
         const double binv = 1.0 / beta;
 #pragma unroll
@@ -511,12 +712,12 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) gmres_kernel(const Solv
                 ctl[1] = c1;
                 ctl[2] = c2;
             }
-            __syncthreads();
+            tm.sync();
             k = ctl[0];
             singular = ctl[1];
             estimate_ok = ctl[2];
-            __syncthreads();  // ctl is rewritten by thread 0 in the next step
-            if (singular || estimate_ok || it >= P.max_iters) break;
+            tm.sync();  // ctl is rewritten by thread 0 in the next step
+            if (singular || estimate_ok || it >= C.max_iters) break;
             const double hinv = 1.0 / hn;
             double* vn = V + (size_t)(j + 1) * vstride;
 #pragma unroll
@@ -534,7 +735,7 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) gmres_kernel(const Solv
                 y[i] = sum / H[i * m + i];
             }
         }
-        __syncthreads();
+        tm.sync();
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int row = tm.row(q);
@@ -548,12 +749,29 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) gmres_kernel(const Solv
         if (!finite(beta2)) { status = ST_NAN; break; }
         if (beta2 <= tau2) { status = ST_CONVERGED; break; }
         if (singular) { status = ST_BREAKDOWN; break; }
-        if (it >= P.max_iters) { status = ST_MAX_ITER; break; }
+        if (it >= C.max_iters) { status = ST_MAX_ITER; break; }
         if (estimate_ok && ++restarts > kMaxRestarts) { status = ST_MAX_ITER; break; }
     }
     double res2 = beta2;
     if (status == ST_NAN) res2 = true_residual(op, b, x, r, sm.xa, sm.red, parity, tm, n);
-    write_result(P, sys, x, status, it, sqrt(res2 / nb2), 0, tm);
+    write_result(io, x, status, it, sqrt(res2 / nb2), 0, tm);
 }
+
+// ----------------------------------------------------- one block per system
+
+#define BBS_UNIFORM_KERNEL(NAME, SYSTEM)                                                       \
+    template <int FMT, int R>                                                                  \
+    __global__ void __launch_bounds__(max_threads_for(R), 1) NAME(const SolveParams P) {       \
+        extern __shared__ __align__(16) unsigned char raw[];                                   \
+        const Team tm = Team::block();                                                         \
+        const int sys = blockIdx.x;                                                            \
+        const auto op = make_op<FMT, R>(P, sys, raw, tm);                                      \
+        SYSTEM<FMT, R>(op, sys_io(P, sys), solve_cfg(P, sys), team_smem(raw, P.n_pad), tm);    \
+    }
+
+BBS_UNIFORM_KERNEL(bicgstab_kernel, bicgstab_any)
+BBS_UNIFORM_KERNEL(cg_kernel, cg_system)
+BBS_UNIFORM_KERNEL(gmres_kernel, gmres_system)
+#undef BBS_UNIFORM_KERNEL
 
 }  // namespace bbs

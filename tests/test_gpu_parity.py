@@ -211,15 +211,19 @@ def test_staging_chunking_order_and_host_path_bitwise(bbs, handle):
     A = wl.matrix("csr")
     base = gpu_solve(bbs, handle, A, wl.b, values_in_smem=-1)
     st = gpu_solve(bbs, handle, A, wl.b, values_in_smem=1)
-    assert np.array_equal(base[0], st[0]) and np.array_equal(base[1], st[1])
-    parts = [gpu_solve(bbs, handle, A.subset(np.arange(c, c + 256)), wl.b[c:c + 256])
+    # staged values run BiCGSTAB with Jacobi folded into the matrix: the same
+    # method up to rounding, so the parity bar applies rather than bit equality
+    fails = compare(*st[:4], base[0], base[1], base[3], label="staged vs streamed")
+    assert not fails, "\n".join(fails)
+    base = st
+    parts = [gpu_solve(bbs, handle, A.subset(np.arange(c, c + 256)), wl.b[c:c + 256], values_in_smem=1)
              for c in range(0, 1024, 256)]
     assert np.array_equal(np.concatenate([p[0] for p in parts]), base[0])
     perm = np.random.default_rng(5).permutation(1024)
-    pr = gpu_solve(bbs, handle, A.subset(perm), wl.b[perm])
+    pr = gpu_solve(bbs, handle, A.subset(perm), wl.b[perm], values_in_smem=1)
     assert np.array_equal(pr[0], base[0][perm]) and np.array_equal(pr[1], base[1][perm])
-    again = gpu_solve(bbs, handle, A, wl.b)
-    assert np.array_equal(again[0], gpu_solve(bbs, handle, A, wl.b)[0])
+    again = gpu_solve(bbs, handle, A, wl.b, values_in_smem=1)
+    assert np.array_equal(again[0], base[0])
     # host-buffer entry point
     hA = bbs.DeviceBatch.from_batch(A, "cpu", pin=True)
     hb = torch.as_tensor(wl.b).pin_memory()

@@ -1,0 +1,123 @@
+"""The persistent, graph-captured uneven-batch solve against the CPU oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_08417_gb300 import workloads as W
+from tests.parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bbs():
+    from paper_2308_08417_gb300 import _build, bbs as mod
+
+    _build.build()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def handle(bbs):
+    return bbs.Handle(0)
+
+
+@pytest.fixture(scope="module")
+def uneven():
+    return W.uneven(3000)
+
+
+
+def run_plan(bbs, plan, vb):
+    b = torch.as_tensor(vb.b, device="cuda")
+    x = torch.as_tensor(vb.x0, device="cuda").clone()
+    log = bbs.Log.empty(vb.num_batch)
+    plan.solve(b, x, log)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), log.iters.cpu().numpy(), log.rel_res.cpu().numpy(), log.status.cpu().numpy()
+
+
+def check_against_oracle(vb, got, solver="bicgstab", sample=400):
+    idx = np.random.default_rng(11).choice(vb.num_batch, min(sample, vb.num_batch), replace=False)
+    xr, itr, relr, str_ = oracle.solve_varsize(vb, solver=solver, systems=idx)
+    x, it, rel, st = got
+    fails = []
+    for k, i in enumerate(idx):
+        o, n = int(vb.vec_off[i]), int(vb.sys_n()[i])
+        f = compare(x[None, o:o + n], it[i:i + 1], rel[i:i + 1], st[i:i + 1], xr[None, o:o + n],
+                    itr[k:k + 1], str_[k:k + 1], label=f"system {i} (n={n})")
+        fails += f
+    return fails
+
+
+def test_default_plan_matches_oracle(bbs, handle, uneven):
+    vbd = bbs.VarDeviceBatch.from_varbatch(uneven)
+    plan = bbs.VarPlan(handle, vbd, bbs.bbs_default_options())
+    got = run_plan(bbs, plan, uneven)
+    assert (got[3] == 0).all()
+    fails = check_against_oracle(uneven, got)
+    assert not fails, "\n".join(fails[:10])
+    # graph replay: the same plan run again gives the same bits
+    again = run_plan(bbs, plan, uneven)
+    assert np.array_equal(again[0], got[0]) and np.array_equal(again[1], got[1])
+
+
+def test_tuned_plans_match_oracle(bbs, handle, uneven):
+    vbd = bbs.VarDeviceBatch.from_varbatch(uneven)
+    b = torch.as_tensor(uneven.b, device="cuda")
+    x0 = torch.as_tensor(uneven.x0, device="cuda")
+    opts = bbs.bbs_default_options()
+    tuning = bbs.bbs_var_tune(handle, vbd, b, x0, opts, sample=128)
+    d = tuning.as_dict()
+    assert d["block_warps"] in (8, 16) and all(w in (1, 2, 4, 8, 16) for w in d["team_warps"])
+    assert np.array_equal(x0.cpu().numpy(), uneven.x0)  # the tuner leaves x0 alone
+    plan = bbs.VarPlan(handle, vbd, opts, tuning)
+    got = run_plan(bbs, plan, uneven)
+    fails = check_against_oracle(uneven, got)
+    assert not fails, "\n".join(fails[:10])
+    # every explicit team size / staging / block shape meets the same bar
+    for bw in (8, 16):
+        for stage in (0, 1):
+            t = bbs.bbs_var_default_tuning(1024)
+            t.block_warps = bw
+            for k in range(t.num_buckets):
+                t.stage_values[k] = stage
+                t.team_warps[k] = min(bw, 2 ** k // 2 or 1)
+            plan = bbs.VarPlan(handle, vbd, opts, t)
+            got = run_plan(bbs, plan, uneven)
+            fails = check_against_oracle(uneven, got, sample=150)
+            assert not fails, f"bw={bw} stage={stage}\n" + "\n".join(fails[:10])
+
+
+def test_cg_on_symmetric_uneven_batch(bbs, handle):
+    vb = W.uneven(500, n_max=600)
+    # symmetrise each system's values in place (same recipe as the CG workload)
+    for pi, p in enumerate(vb.patterns):
+        members = np.nonzero(vb.sys_pattern == pi)[0]
+        if len(members) == 0:
+            continue
+        rng = np.random.default_rng(pi)
+        vals = W.stencil_values(p, len(members), rng, 0.05, 0.5, symmetric=True)
+        for k, i in enumerate(members):
+            vb.values[int(vb.val_off[i]):int(vb.val_off[i]) + p.nnz] = vals[k]
+    vbd = bbs.VarDeviceBatch.from_varbatch(vb)
+    plan = bbs.VarPlan(handle, vbd, bbs.bbs_default_options(solver="cg"))
+    got = run_plan(bbs, plan, vb)
+    fails = check_against_oracle(vb, got, solver="cg", sample=200)
+    assert not fails, "\n".join(fails[:10])
+
+
+def test_plan_argument_errors(bbs, handle, uneven):
+    vbd = bbs.VarDeviceBatch.from_varbatch(uneven)
+    for kw in (dict(solver="gmres"), dict(precision="mixed"), dict(tol=0.0)):
+        with pytest.raises(bbs.BBSError):
+            bbs.VarPlan(handle, vbd, bbs.bbs_default_options(**kw))
+    t = bbs.bbs_var_default_tuning(1024)
+    t.block_warps = 12
+    with pytest.raises(bbs.BBSError):
+        bbs.VarPlan(handle, vbd, bbs.bbs_default_options(), t)
+    t = bbs.bbs_var_default_tuning(256)  # buckets stop at 256: larger systems rejected
+    with pytest.raises(bbs.BBSError):
+        bbs.VarPlan(handle, vbd, bbs.bbs_default_options(), t)
