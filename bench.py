@@ -50,9 +50,9 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 
 # dram bytes (read + write) per launch of a kernel from an ncu capture of it,
 # scaled to the benchmark's launch; an entry is removed when its kernel changes.
-# bicgstab_kernel: profiles/bicgstab_kernel_stencil2d5_n144.md, 280.0 MB for
-# 32,768 systems -> 560 MB for the 65,536-system launch.
-TRAFFIC_BYTES = {"bicgstab_kernel": 560.0e6}
+# bicgstab_folded_kernel: profiles/bicgstab_folded_kernel_stencil2d5_n144.md,
+# 280.8 MB for 32,768 systems -> 561.5 MB for the 65,536-system launch.
+TRAFFIC_BYTES = {"bicgstab_folded_kernel": 561.5e6}
 
 
 def parse():
@@ -140,7 +140,8 @@ class Uniform:
         self.log = bbs.Log.empty(wl.num_batch, device=dev, inner=self.mixed)
         self.ws = self.h.workspace(self.dA, self.opts)
         self.num_batch = wl.num_batch
-        self.kernel = "refine_kernel" if self.mixed else "bicgstab_kernel"
+        # BiCGSTAB + Jacobi with staged values runs the Jacobi-folded kernel
+        self.kernel = "refine_kernel" if self.mixed else "bicgstab_folded_kernel"
         self.launches_per_step = 2 if (self.mixed and self.ws is not None) else 1
 
     def reset(self):

@@ -276,14 +276,18 @@ bbs_status bbs_var_tune(bbs_handle *handle, const bbs_var_batch *batch,
  * from whatever guess it is given.
  * Parameter layout (FP32, flat): W1 b1 W2 b2 W3 b3 W4 b4, W_l row-major
  * [out, in] (y = x W^T + b); W1 is [hidden, 3n], W4 is [n, hidden].
- * Feature rows (BF16, stored as uint16_t) have ceil(3n/32)*32 columns:
+ * Feature rows (BF16, stored as uint16_t) have ceil(3n/64)*64 columns:
  * standardised diag(A) (n), b (n), x_prev (n), then zeros.
  * ------------------------------------------------------------------------ */
 typedef struct bbs_mlp bbs_mlp;
 
+/* Tensor-core paths of the network's GEMMs: tcgen05 MMAs with the FP32
+ * accumulator in tensor memory (K-tiles of 64), or warp-level mma.sync. */
+typedef enum { BBS_GEMM_MMA_SYNC = 0, BBS_GEMM_TCGEN05 = 1 } bbs_gemm_kind;
+
 /* Create a network for systems of n rows (1..2048) with `hidden` units (a
- * multiple of 32, 32..4096) and minibatches of up to max_batch rows (a
- * multiple of 32). Weights are drawn from U(-1/sqrt(in), 1/sqrt(in)) by a
+ * multiple of 64, 64..4096) and minibatches of up to max_batch rows (a
+ * multiple of 64). Weights are drawn from U(-1/sqrt(in), 1/sqrt(in)) by a
  * counter-based hash of `seed` (output layer scaled by 0.1), biases zero.
  * Allocates all its device buffers here. */
 bbs_status bbs_mlp_create(bbs_handle *handle, int32_t n, int32_t hidden, uint64_t seed,
@@ -301,13 +305,13 @@ bbs_status bbs_mlp_observe(bbs_mlp *mlp, const bbs_batch_matrix *A, const double
                            const double *x_prev, const double *x_next, void *stream);
 /* Turn the accumulated moments into the standardisation (mean, std). */
 bbs_status bbs_mlp_finalize_stats(bbs_mlp *mlp, void *stream);
-/* Standardised feature rows [num_batch, ceil(3n/32)*32] (BF16) and, when
+/* Standardised feature rows [num_batch, ceil(3n/64)*64] (BF16) and, when
  * x_next is given, standardised targets [num_batch, n] (FP32), DEVICE. */
 bbs_status bbs_mlp_make_samples(bbs_mlp *mlp, const bbs_batch_matrix *A, const double *b,
                                 const double *x_prev, const double *x_next, uint16_t *feats,
                                 float *targets, void *stream);
 /* Loss and parameter gradients of the minibatch made of rows `rows` (DEVICE
- * int32 [M]) of the sample store (feats, targets); M a multiple of 32 up to
+ * int32 [M]) of the sample store (feats, targets); M a multiple of 64 up to
  * max_batch. *loss (DEVICE) receives the mean squared error; the gradients
  * stay in the network (flat layout, see bbs_mlp_get_grads). */
 bbs_status bbs_mlp_gradients(bbs_mlp *mlp, const uint16_t *feats, const float *targets,
@@ -315,6 +319,18 @@ bbs_status bbs_mlp_gradients(bbs_mlp *mlp, const uint16_t *feats, const float *t
 /* bbs_mlp_gradients followed by one Adam step with learning rate lr. */
 bbs_status bbs_mlp_train_step(bbs_mlp *mlp, const uint16_t *feats, const float *targets,
                               const int32_t *rows, int32_t M, float lr, float *loss, void *stream);
+/* Choose the tensor-core path of the network's GEMMs (default mma.sync). */
+bbs_status bbs_mlp_set_gemm(bbs_mlp *mlp, int32_t kind);
+/* Wait for the network's work and report whether a tcgen05 GEMM gave up on
+ * a bounded wait (BBS_ERR_CUDA) since creation. */
+bbs_status bbs_mlp_check(bbs_mlp *mlp);
+/* C[m][n] = sum_k A[m*lda + k] B[n*ldb + k] for BF16 A [M, K] and B [N, K]
+ * (both K-contiguous, DEVICE), FP32 C [M, ldc] (DEVICE), through the chosen
+ * tensor-core path; K a multiple of 64 (tcgen05) or 32 (mma.sync), lda and
+ * ldb multiples of 8. Synchronous; the building block of the network. */
+bbs_status bbs_gemm_bf16(bbs_handle *handle, int32_t kind, const uint16_t *A, int32_t lda,
+                         const uint16_t *B, int32_t ldb, int32_t M, int32_t N, int32_t K, float *C,
+                         int32_t ldc);
 /* Copy the gradients (flat layout) of the last bbs_mlp_gradients /
  * bbs_mlp_train_step to a DEVICE array. Asynchronous on stream. */
 bbs_status bbs_mlp_get_grads(bbs_mlp *mlp, float *grads, void *stream);

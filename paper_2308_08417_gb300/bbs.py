@@ -23,6 +23,7 @@ PRECOND = {"none": 0, "jacobi": 1}
 TOL = {"absolute": 0, "relative": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 SYS_STATUS = {0: "converged", 1: "max_iter", 2: "breakdown", 3: "nan"}
+GEMM = {"mma": 0, "tcgen05": 1}
 
 
 class bbs_batch_matrix(C.Structure):
@@ -122,6 +123,9 @@ def lib():
         L.bbs_mlp_train_step.argtypes = [vp, vp, vp, vp, i32, C.c_float, vp, st]
         L.bbs_mlp_forward.argtypes = [vp, vp, i32, vp, st]
         L.bbs_mlp_predict.argtypes = [vp, P(bbs_batch_matrix), vp, vp, vp, st]
+        L.bbs_mlp_set_gemm.argtypes = [vp, i32]
+        L.bbs_mlp_check.argtypes = [vp]
+        L.bbs_gemm_bf16.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, i32, vp, i32]
         L.bbs_paper_block_size.argtypes = [C.c_int32, C.c_int32]
         L.bbs_paper_block_size.restype = C.c_int32
         L.bbs_default_block_size.argtypes = [C.c_int32, C.c_int32]
@@ -134,7 +138,8 @@ def lib():
                      "bbs_mlp_create", "bbs_mlp_destroy", "bbs_mlp_param_count", "bbs_mlp_get_params",
                      "bbs_mlp_set_params", "bbs_mlp_get_grads", "bbs_mlp_observe",
                      "bbs_mlp_finalize_stats", "bbs_mlp_make_samples", "bbs_mlp_gradients",
-                     "bbs_mlp_train_step", "bbs_mlp_forward", "bbs_mlp_predict"):
+                     "bbs_mlp_train_step", "bbs_mlp_forward", "bbs_mlp_predict", "bbs_mlp_set_gemm",
+                     "bbs_mlp_check", "bbs_gemm_bf16"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -429,7 +434,7 @@ class MLP:
         self._p = p
         self._handle = handle
         self.n, self.hidden, self.max_batch = int(n), int(hidden), int(max_batch)
-        self.in_pad = (3 * self.n + 31) // 32 * 32
+        self.in_pad = (3 * self.n + 63) // 64 * 64
         cnt = C.c_int64()
         _check(lib().bbs_mlp_param_count(p, C.byref(cnt)), "bbs_mlp_param_count")
         self.param_count = int(cnt.value)
@@ -445,6 +450,12 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+    def set_gemm(self, kind: str):
+        _check(lib().bbs_mlp_set_gemm(self._p, GEMM[kind]), "bbs_mlp_set_gemm")
+
+    def check(self):
+        _check(lib().bbs_mlp_check(self._p), "bbs_mlp_check")
 
     def get_params(self) -> torch.Tensor:
         out = torch.empty(self.param_count, dtype=torch.float32, device=self.device)
@@ -504,3 +515,13 @@ class MLP:
         _check(lib().bbs_mlp_predict(self._p, C.byref(s), _ptr(b), _ptr(x_prev), _ptr(x0), _stream(b)),
                "bbs_mlp_predict")
         return x0
+
+
+def bbs_gemm_bf16(handle: Handle, kind: str, A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """C = A B^T (A [M, K], B [N, K] bfloat16 on the device) through a tensor-core path."""
+    M, K = A.shape
+    N = B.shape[0]
+    C_ = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    _check(lib().bbs_gemm_bf16(handle._h, GEMM[kind], _ptr(A), A.stride(0), _ptr(B), B.stride(0), M, N, K,
+                               _ptr(C_), N), "bbs_gemm_bf16")
+    return C_

@@ -164,12 +164,15 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
 
 size_t workspace_bytes(const Plan& p) { return align_up(p.ws_gmres, 256) + p.ws_f32; }
 
-const void* pick_kernel(const bbs_options* o, int fmt, int R) {
+// BiCGSTAB with staged values and Jacobi runs the Jacobi-folded kernel.
+const void* pick_kernel(const bbs_options* o, int fmt, int R, bool staged) {
     if (o->precision == BBS_PRECISION_MIXED_IR) return bbs::refine_fn(fmt, R);
     switch (o->solver) {
         case BBS_SOLVER_CG: return bbs::cg_fn(fmt, R);
         case BBS_SOLVER_GMRES: return bbs::gmres_fn(fmt, R);
-        default: return bbs::bicgstab_fn(fmt, R);
+        default:
+            return (staged && o->precond == BBS_PREC_JACOBI) ? bbs::bicgstab_folded_fn(fmt, R)
+                                                             : bbs::bicgstab_fn(fmt, R);
     }
 }
 
@@ -325,7 +328,7 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
             return cuda_fail(e, "FP32 conversion launch");
         P.values32 = f32;
     }
-    const void* fn = pick_kernel(o, A->fmt, p.R);
+    const void* fn = pick_kernel(o, A->fmt, p.R, p.stage);
     if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     void* args[] = {&P};
     e = cudaLaunchKernel(fn, dim3((unsigned)A->num_batch), dim3((unsigned)p.threads), args, p.smem, st);

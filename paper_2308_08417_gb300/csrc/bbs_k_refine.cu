@@ -39,6 +39,7 @@ cudaError_t launch_convert_f32(const double* src, float* dst, size_t count, cuda
         return S##_fn_dense(R);                        \
     }
 BBS_FRONT(bicgstab)
+BBS_FRONT(bicgstab_folded)
 BBS_FRONT(cg)
 BBS_FRONT(gmres)
 BBS_FRONT(refine)

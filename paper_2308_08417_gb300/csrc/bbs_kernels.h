@@ -22,6 +22,7 @@ constexpr int kMaxRows = 2048;
     const void* S##_fn_ell(int R);       \
     const void* S##_fn_dense(int R);
 BBS_DECL(bicgstab)
+BBS_DECL(bicgstab_folded)
 BBS_DECL(cg)
 BBS_DECL(gmres)
 BBS_DECL(refine)

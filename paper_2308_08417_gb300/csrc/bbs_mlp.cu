@@ -29,6 +29,7 @@
 #include "../../include/bbs.h"
 #include "bbs_internal.h"
 #include "bbs_mlp_gemm.cuh"
+#include "bbs_umma.cuh"
 
 namespace bbs {
 namespace mlp {
@@ -92,6 +93,12 @@ __global__ void __launch_bounds__(256) gemm_kernel(const __nv_bfloat16* __restri
                                                    const __nv_bfloat16* __restrict__ B, int ldb, int M,
                                                    int N, int K, Epi epi) {
     gemm_tn_mma<Epi>(A, lda, B, ldb, M, N, K, epi);
+}
+
+__global__ void __launch_bounds__(128, 1) gemm_umma_kernel(const __nv_bfloat16* __restrict__ A, int lda,
+                                                           const __nv_bfloat16* __restrict__ B, int ldb,
+                                                           int M, int N, int K, int BN, Epi epi, int* err) {
+    umma::gemm_tn_umma<Epi>(A, lda, B, ldb, M, N, K, BN, epi, err);
 }
 
 // ---------------------------------------------------- small kernels
@@ -317,6 +324,8 @@ struct bbs_mlp {
     __nv_bfloat16* DZ[3] = {};
     __nv_bfloat16* DZT[3] = {};
     int32_t* idx = nullptr;
+    int* err = nullptr;     // set by a tensor-core GEMM whose waits ran out
+    int gemm_kind = 0;      // BBS_GEMM_MMA_SYNC or BBS_GEMM_TCGEN05
     std::vector<void*> allocs;
 };
 
@@ -343,11 +352,33 @@ bool dev_alloc(bbs_mlp* m, T** ptr, size_t count) {
     return true;
 }
 
-cudaError_t gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
-                 const Epi& e, cudaStream_t st) {
+// C = A B^T through the chosen tensor-core path (kind 1: tcgen05 with the
+// accumulator in tensor memory, K a multiple of 64; kind 0: mma.sync).
+cudaError_t gemm_any(int kind, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
+                     int K, const Epi& e, int* err, cudaStream_t st) {
+    if (kind == BBS_GEMM_TCGEN05) {
+        const int BN = std::min(256, round_up(N, 16));
+        const size_t smem = bbs::umma::smem_bytes(BN);
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t a = cudaFuncSetAttribute(bbs::mlp::gemm_umma_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)bbs::umma::smem_bytes(256));
+            if (a != cudaSuccess) return a;
+            attr_set = true;
+        }
+        dim3 grid((N + BN - 1) / BN, (M + bbs::umma::kBM - 1) / bbs::umma::kBM);
+        bbs::mlp::gemm_umma_kernel<<<grid, 128, smem, st>>>(A, lda, B, ldb, M, N, K, BN, e, err);
+        return cudaGetLastError();
+    }
     dim3 grid((N + bbs::mlp::kBN - 1) / bbs::mlp::kBN, (M + bbs::mlp::kBM - 1) / bbs::mlp::kBM);
     bbs::mlp::gemm_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, K, e);
     return cudaGetLastError();
+}
+
+cudaError_t gemm(bbs_mlp* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
+                 int K, const Epi& e, cudaStream_t st) {
+    return gemm_any(m->gemm_kind, A, lda, B, ldb, M, N, K, e, m->err, st);
 }
 
 Epi epi_f32(float* c, int ldc) {
@@ -382,7 +413,7 @@ cudaError_t forward(bbs_mlp* m, const __nv_bfloat16* X, int M, bool keep_transpo
         ep.ldy = m->hidden;
         ep.yt = keep_transposed ? m->YT[l] : nullptr;
         ep.ldyt = M;
-        e = gemm(h, ldh, m->Wb[l], m->pad_in[l], M, m->hidden, m->pad_in[l], ep, st);
+        e = gemm(m, h, ldh, m->Wb[l], m->pad_in[l], M, m->hidden, m->pad_in[l], ep, st);
         h = m->Y[l];
         ldh = m->hidden;
     }
@@ -392,7 +423,7 @@ cudaError_t forward(bbs_mlp* m, const __nv_bfloat16* X, int M, bool keep_transpo
     ep.c = m->out;
     ep.ldc = m->n;
     ep.bias = m->p + m->off_b[3];
-    return gemm(h, ldh, m->Wb[3], m->pad_in[3], M, m->n, m->pad_in[3], ep, st);
+    return gemm(m, h, ldh, m->Wb[3], m->pad_in[3], M, m->n, m->pad_in[3], ep, st);
 }
 
 // Loss and gradients of the minibatch in X/XT/T (M rows) into m->g.
@@ -409,7 +440,7 @@ cudaError_t backward(bbs_mlp* m, int M, float* loss, cudaStream_t st) {
         const int out = m->dims_out[l], in = m->dims_in[l];
         // dW_l = d^T [out, M] . h_{l-1}^T [in, M]^T  -> [out, in]
         const __nv_bfloat16* hT = (l == 0) ? m->XT : m->YT[l - 1];
-        if ((e = gemm(dT, M, hT, M, out, in, M, epi_f32(m->g + m->off_W[l], in), st)) != cudaSuccess) return e;
+        if ((e = gemm(m, dT, M, hT, M, out, in, M, epi_f32(m->g + m->off_W[l], in), st)) != cudaSuccess) return e;
         bias_grad_kernel<<<(out + 7) / 8, 256, 0, st>>>(out, M, dT, m->g + m->off_b[l]);
         if (l == 0) break;
         // d_{l-1} = (d . W_l) * gelu'(z_{l-1}):  [M, in] = d [M, out_pad] . W_l^T [in, out_pad]^T
@@ -421,7 +452,7 @@ cudaError_t backward(bbs_mlp* m, int M, float* loss, cudaStream_t st) {
         ep.ldy = m->hidden;
         ep.yt = m->DZT[l - 1];
         ep.ldyt = M;
-        if ((e = gemm(d, ld_d, m->WTb[l], m->pad_out[l], M, in, m->pad_out[l], ep, st)) != cudaSuccess) return e;
+        if ((e = gemm(m, d, ld_d, m->WTb[l], m->pad_out[l], M, in, m->pad_out[l], ep, st)) != cudaSuccess) return e;
         d = m->DZ[l - 1];
         dT = m->DZT[l - 1];
         ld_d = m->hidden;
@@ -437,26 +468,26 @@ bbs_status bbs_mlp_create(bbs_handle* h, int32_t n, int32_t hidden, uint64_t see
                           bbs_mlp** out) {
     if (h == nullptr || out == nullptr) return errf(BBS_ERR_INVALID_ARG, "null handle or output");
     *out = nullptr;
-    if (n < 1 || n > 2048 || hidden < 32 || hidden % 32 != 0 || hidden > 4096)
-        return errf(BBS_ERR_INVALID_ARG, "need 1 <= n <= 2048 and hidden a multiple of 32 in [32, 4096]");
-    if (max_batch < 32 || max_batch % 32 != 0)
-        return errf(BBS_ERR_INVALID_ARG, "max_batch must be a positive multiple of 32");
+    if (n < 1 || n > 2048 || hidden < 64 || hidden % 64 != 0 || hidden > 4096)
+        return errf(BBS_ERR_INVALID_ARG, "need 1 <= n <= 2048 and hidden a multiple of 64 in [64, 4096]");
+    if (max_batch < 64 || max_batch % 64 != 0)
+        return errf(BBS_ERR_INVALID_ARG, "max_batch must be a positive multiple of 64");
     cudaSetDevice(bbs::handle_device(h));
     bbs_mlp* m = new bbs_mlp();
     m->device = bbs::handle_device(h);
     m->n = n;
     m->hidden = hidden;
     m->in = 3 * n;
-    m->in_pad = round_up(3 * n, 32);
-    m->n_pad = round_up(n, 32);
+    m->in_pad = round_up(3 * n, 64);
+    m->n_pad = round_up(n, 64);
     m->max_batch = max_batch;
     const int ins[4] = {3 * n, hidden, hidden, hidden}, outs[4] = {hidden, hidden, hidden, n};
     size_t o = 0;
     for (int l = 0; l < 4; ++l) {
         m->dims_in[l] = ins[l];
         m->dims_out[l] = outs[l];
-        m->pad_in[l] = round_up(ins[l], 32);
-        m->pad_out[l] = round_up(outs[l], 32);
+        m->pad_in[l] = round_up(ins[l], 64);
+        m->pad_out[l] = round_up(outs[l], 64);
         m->off_W[l] = o;
         o += (size_t)ins[l] * outs[l];
         m->off_b[l] = o;
@@ -475,7 +506,7 @@ bbs_status bbs_mlp_create(bbs_handle* h, int32_t n, int32_t hidden, uint64_t see
     ok = ok && dev_alloc(m, &m->X, MB * m->in_pad) && dev_alloc(m, &m->XT, MB * m->in_pad) &&
          dev_alloc(m, &m->T, MB * n) && dev_alloc(m, &m->out, MB * n) &&
          dev_alloc(m, &m->D, MB * m->n_pad) && dev_alloc(m, &m->DT, MB * m->n_pad) &&
-         dev_alloc(m, &m->idx, MB);
+         dev_alloc(m, &m->idx, MB) && dev_alloc(m, &m->err, 1);
     for (int l = 0; l < 3 && ok; ++l)
         ok = dev_alloc(m, &m->Z[l], MB * hidden) && dev_alloc(m, &m->Y[l], MB * hidden) &&
              dev_alloc(m, &m->YT[l], MB * hidden) && dev_alloc(m, &m->DZ[l], MB * hidden) &&
@@ -584,8 +615,8 @@ bbs_status bbs_mlp_make_samples(bbs_mlp* m, const bbs_batch_matrix* A, const dou
 bbs_status bbs_mlp_gradients(bbs_mlp* m, const uint16_t* feats, const float* targets, const int32_t* rows,
                              int32_t M, float* loss, void* stream) {
     if (m == nullptr || !feats || !targets || !rows || !loss) return errf(BBS_ERR_INVALID_ARG, "null argument");
-    if (M < 32 || M > m->max_batch || M % 32 != 0)
-        return errf(BBS_ERR_INVALID_ARG, "minibatch must be a multiple of 32 up to %d", m->max_batch);
+    if (M < 64 || M > m->max_batch || M % 64 != 0)
+        return errf(BBS_ERR_INVALID_ARG, "minibatch must be a multiple of 64 up to %d", m->max_batch);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaMemcpyAsync(m->idx, rows, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st);
     bbs::mlp::gather_kernel<<<M, 128, 0, st>>>(M, m->in_pad, m->n, m->idx,
@@ -608,6 +639,50 @@ bbs_status bbs_mlp_train_step(bbs_mlp* m, const uint16_t* feats, const float* ta
     pack_all(m, st);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? BBS_OK : errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
+}
+
+bbs_status bbs_mlp_set_gemm(bbs_mlp* m, int32_t kind) {
+    if (m == nullptr || (kind != BBS_GEMM_MMA_SYNC && kind != BBS_GEMM_TCGEN05))
+        return errf(BBS_ERR_INVALID_ARG, "unknown GEMM kind");
+    m->gemm_kind = kind;
+    return BBS_OK;
+}
+
+bbs_status bbs_mlp_check(bbs_mlp* m) {
+    if (m == nullptr) return errf(BBS_ERR_INVALID_ARG, "null network");
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, m->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
+    return flag ? errf(BBS_ERR_CUDA, "a tensor-core GEMM gave up waiting for its MMAs") : BBS_OK;
+}
+
+bbs_status bbs_gemm_bf16(bbs_handle* h, int32_t kind, const uint16_t* A, int32_t lda, const uint16_t* B,
+                         int32_t ldb, int32_t M, int32_t N, int32_t K, float* C, int32_t ldc) {
+    if (h == nullptr || !A || !B || !C || M < 0 || N < 0 || K < 0)
+        return errf(BBS_ERR_INVALID_ARG, "null pointer or negative size");
+    if (kind != BBS_GEMM_MMA_SYNC && kind != BBS_GEMM_TCGEN05) return errf(BBS_ERR_INVALID_ARG, "unknown GEMM kind");
+    const int kmul = kind == BBS_GEMM_TCGEN05 ? 64 : 32;
+    if (K % kmul != 0 || lda % 8 != 0 || ldb % 8 != 0 || lda < K || ldb < K || ldc < N)
+        return errf(BBS_ERR_INVALID_ARG, "K must be a multiple of %d, lda/ldb multiples of 8 and >= K", kmul);
+    if (M == 0 || N == 0) return BBS_OK;
+    cudaSetDevice(bbs::handle_device(h));
+    int* err = nullptr;
+    cudaError_t e = cudaMalloc(&err, sizeof(int));
+    if (e != cudaSuccess) return errf(BBS_ERR_NO_MEMORY, "%s", cudaGetErrorString(e));
+    cudaMemset(err, 0, sizeof(int));
+    Epi ep = epi_f32(C, ldc);
+    if (K == 0) {
+        cudaFree(err);
+        return errf(BBS_ERR_INVALID_ARG, "K must be positive");
+    }
+    e = gemm_any(kind, reinterpret_cast<const __nv_bfloat16*>(A), lda, reinterpret_cast<const __nv_bfloat16*>(B),
+                 ldb, M, N, K, ep, err, nullptr);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
+    return flag ? errf(BBS_ERR_CUDA, "the tensor-core GEMM gave up waiting for its MMAs") : BBS_OK;
 }
 
 bbs_status bbs_mlp_get_grads(bbs_mlp* m, float* grads, void* stream) {

@@ -334,43 +334,77 @@ __device__ __forceinline__ void scale_columns(const Mat<double>& A, double* as, 
 // plain BiCGSTAB on As x~ = b (p^ = D^-1 p and s^ = D^-1 s never need forming;
 // x~ += alpha p + omega s). Same iterates as bicgstab_system up to rounding,
 // two FP64 multiplies per row and iteration fewer. Scalar tests run on the
-// integer pipe. x = D^-1 x~ on exit.
+// integer pipe. Only the six vectors the iteration updates stay in registers
+// (b, x0 and the diagonal are re-read from memory when needed), which keeps
+// the register count, and so the number of resident systems, up. x = D^-1 x~
+// on exit; a system that takes no iteration returns its x0 untouched.
+template <int FMT, int R>
+__device__ __forceinline__ double residual_from_global(const Op<FMT, R, double, double>& op,
+                                                       const double* __restrict__ bg,
+                                                       const double (&x)[R], double (&r)[R],
+                                                       double* xs, double* red, int& parity,
+                                                       const Team& tm, int n) {
+    put(xs, x, tm, n);
+    tm.sync();
+    double ax[R];
+    op.apply(xs, ax, tm);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        r[q] = (row < n ? bg[row] : 0.0) - ax[q];
+    }
+    double s[1] = {pdot(r, r)};
+    block_sum(s, red, parity, tm);
+    return s[0];
+}
+
 template <int FMT, int R>
 __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, double>& op,
                                                        const SysIO& io, const SolveCfg& C,
                                                        const TeamSmem& sm, const Team& tm) {
     const int n = io.n;
     int parity = 0;
-    double b[R], x0[R], xs[R], r[R], rh[R], p[R], v[R], dinv[R], t[R];
-    load_system<R>(io, b, x0, tm);
-    jacobi_setup<FMT, R>(op.A, true, dinv, tm);
+    double xs[R], r[R], rh[R], p[R], v[R], t[R];
+    {
+        double dinv[R];
+        jacobi_setup<FMT, R>(op.A, true, dinv, tm);
+        scale_columns<FMT, R>(op.A, const_cast<double*>(op.as), dinv, sm.xb, tm);
+    }
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
+    for (int q = 0; q < R; ++q) {  // x~ = D x0 (1 for a zero diagonal)
         const int row = tm.row(q);
         const double d = row < n ? diag_entry<FMT>(op.A, row) : 0.0;
-        xs[q] = (d != 0.0) ? d * x0[q] : x0[q];  // x~ = D x (1 for a zero diagonal)
+        const double x0 = row < n ? io.x[row] : 0.0;
+        xs[q] = (d != 0.0) ? d * x0 : x0;
     }
-    scale_columns<FMT, R>(op.A, const_cast<double*>(op.as), dinv, sm.xb, tm);
-
-    put(sm.xa, xs, tm, n);
-    tm.sync();
-    op.apply(sm.xa, t, tm);
+    double nb2;
+    {
+        double bb = 0.0;
 #pragma unroll
-    for (int q = 0; q < R; ++q) r[q] = b[q] - t[q];
-    double s0[2] = {pdot(b, b), pdot(r, r)};
-    block_sum(s0, sm.red, parity, tm);
-    const double nb2 = s0[0];
-    double rr = s0[1];
-    if (!finite64(nb2)) {
-        write_result(io, x0, ST_NAN, 0, quiet_nan(), 0, tm);
+        for (int q = 0; q < R; ++q) {
+            const int row = tm.row(q);
+            const double bq = row < n ? io.b[row] : 0.0;
+            bb = fma(bq, bq, bb);
+        }
+        double s0[1] = {bb};
+        block_sum(s0, sm.red, parity, tm);
+        nb2 = s0[0];
+    }
+    if (!finite64(nb2)) {  // x stays x0
+        if (tm.tid == 0) {
+            *io.iters = 0;
+            *io.rel_res = quiet_nan();
+            *io.status = ST_NAN;
+        }
         return;
     }
     if (zero64(nb2)) {
 #pragma unroll
-        for (int q = 0; q < R; ++q) x0[q] = 0.0;
-        write_result(io, x0, ST_CONVERGED, 0, 0.0, 0, tm);
+        for (int q = 0; q < R; ++q) xs[q] = 0.0;
+        write_result(io, xs, ST_CONVERGED, 0, 0.0, 0, tm);
         return;
     }
+    double rr = residual_from_global(op, io.b, xs, r, sm.xa, sm.red, parity, tm, n);
     int status = -1, iters = 0;
     double res2 = rr;
     bool have_res = true;
@@ -436,7 +470,7 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
                 candidate = le_nonneg64(rr, tau2);
             }
             if (candidate) {
-                res2 = true_residual(op, b, xs, r, sm.xa, sm.red, parity, tm, n);
+                res2 = residual_from_global(op, io.b, xs, r, sm.xa, sm.red, parity, tm, n);
                 have_res = true;
                 if (!finite64(res2)) { status = ST_NAN; break; }
                 if (le_nonneg64(res2, tau2)) { status = ST_CONVERGED; break; }
@@ -458,12 +492,22 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
         }
         if (status < 0) status = ST_MAX_ITER;
     }
-    if (!have_res) res2 = true_residual(op, b, xs, r, sm.xa, sm.red, parity, tm, n);
-    if (iters > 0) {  // with no iteration the guess is returned unchanged
+    if (!have_res) res2 = residual_from_global(op, io.b, xs, r, sm.xa, sm.red, parity, tm, n);
+    if (iters > 0) {  // x = D^-1 x~ (1 for a zero diagonal)
 #pragma unroll
-        for (int q = 0; q < R; ++q) x0[q] = dinv[q] * xs[q];
+        for (int q = 0; q < R; ++q) {
+            const int row = tm.row(q);
+            if (row >= n) continue;
+            const double d = diag_entry<FMT>(op.A, row);
+            io.x[row] = (d != 0.0) ? xs[q] / d : xs[q];
+        }
     }
-    write_result(io, x0, status, iters, sqrt(res2 / nb2), 0, tm);
+    if (tm.tid == 0) {
+        *io.iters = iters;
+        *io.rel_res = sqrt(res2 / nb2);
+        *io.status = status;
+        if (io.inner != nullptr) *io.inner = 0;
+    }
 }
 
 // BiCGSTAB entry: the folded form when the values are staged and Jacobi is on.
@@ -769,9 +813,23 @@ __device__ __forceinline__ void gmres_system(const Op<FMT, R, double, double>& o
         SYSTEM<FMT, R>(op, sys_io(P, sys), solve_cfg(P, sys), team_smem(raw, P.n_pad), tm);    \
     }
 
-BBS_UNIFORM_KERNEL(bicgstab_kernel, bicgstab_any)
+BBS_UNIFORM_KERNEL(bicgstab_kernel, bicgstab_system)
 BBS_UNIFORM_KERNEL(cg_kernel, cg_system)
 BBS_UNIFORM_KERNEL(gmres_kernel, gmres_system)
 #undef BBS_UNIFORM_KERNEL
 
+// The folded BiCGSTAB keeps six vectors in registers; at 5-6 rows per thread
+// a cap of 128 registers holds them without spilling and doubles the systems
+// an SM keeps resident (the FP64 pipe needs many warps to stay busy).
+__host__ __device__ constexpr int folded_min_blocks(int R) { return (R == 5 || R == 6) ? 2 : 1; }
+
+template <int FMT, int R>
+__global__ void __launch_bounds__(max_threads_for(R), folded_min_blocks(R))
+    bicgstab_folded_kernel(const SolveParams P) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    const Team tm = Team::block();
+    const int sys = blockIdx.x;
+    const auto op = make_op<FMT, R>(P, sys, raw, tm);
+    bicgstab_scaled_system<FMT, R>(op, sys_io(P, sys), solve_cfg(P, sys), team_smem(raw, P.n_pad), tm);
+}
 }  // namespace bbs

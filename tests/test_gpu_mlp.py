@@ -22,10 +22,12 @@ def bbs():
     return mod
 
 
-@pytest.fixture(scope="module")
-def net(bbs):
+@pytest.fixture(scope="module", params=["mma", "tcgen05"])
+def net(bbs, request):
     h = bbs.Handle(0)
-    return bbs.MLP(h, N, hidden=HID, seed=7, max_batch=1024)
+    m = bbs.MLP(h, N, hidden=HID, seed=7, max_batch=1024)
+    m.set_gemm(request.param)
+    return m
 
 
 def sizes():
@@ -52,6 +54,7 @@ def test_forward_matches_oracle(net):
     ref, _ = OM.forward(params, Xb, round_bf16=True)
     rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
     assert rel < 5e-3, rel
+    net.check()
 
 
 def test_gradients_match_oracle(net):
