@@ -319,7 +319,7 @@ bbs_status bbs_mlp_gradients(bbs_mlp *mlp, const uint16_t *feats, const float *t
 /* bbs_mlp_gradients followed by one Adam step with learning rate lr. */
 bbs_status bbs_mlp_train_step(bbs_mlp *mlp, const uint16_t *feats, const float *targets,
                               const int32_t *rows, int32_t M, float lr, float *loss, void *stream);
-/* Choose the tensor-core path of the network's GEMMs (default mma.sync). */
+/* Choose the tensor-core path of the network's GEMMs (default tcgen05). */
 bbs_status bbs_mlp_set_gemm(bbs_mlp *mlp, int32_t kind);
 /* Wait for the network's work and report whether a tcgen05 GEMM gave up on
  * a bounded wait (BBS_ERR_CUDA) since creation. */

@@ -1,7 +1,9 @@
 // Learned initial guess for time-stepped batches: a small MLP that predicts
 // each system's change of solution from its diagonal, right-hand side and
 // previous solution, trained and run on the GPU by this file's kernels
-// (BF16 tensor-core GEMMs with FP32 accumulation, FP32 master weights, Adam).
+// (BF16 tensor-core GEMMs with FP32 accumulation -- tcgen05 MMAs with the
+// accumulator in tensor memory by default, mma.sync as the alternative --
+// FP32 master weights, Adam).
 // The paper has no such network; it motivates it: the solver accepts an
 // initial guess (Sec. 2.1), and a better guess means fewer iterations.
 //
@@ -325,7 +327,7 @@ struct bbs_mlp {
     __nv_bfloat16* DZT[3] = {};
     int32_t* idx = nullptr;
     int* err = nullptr;     // set by a tensor-core GEMM whose waits ran out
-    int gemm_kind = 0;      // BBS_GEMM_MMA_SYNC or BBS_GEMM_TCGEN05
+    int gemm_kind = BBS_GEMM_TCGEN05;  // or BBS_GEMM_MMA_SYNC
     std::vector<void*> allocs;
 };
 
