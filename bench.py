@@ -61,7 +61,8 @@ def parse():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="scale", choices=["scale", "mixed", "uneven", "learned"])
+    p.add_argument("--workload", default="scale",
+                   choices=["scale", "mixed", "uneven", "learned", "pele", "sweep"])
     p.add_argument("--systems", type=int, default=0,
                    help="solve only the first N systems of the workload (profiling runs)")
     p.add_argument("--no-e2e", action="store_true")
@@ -309,6 +310,88 @@ def make_runner(name, bbs, torch, dev, systems=0):
     return Uniform(bbs, torch, dev, wl, "csr", {}, wl.name)
 
 
+def timed_solve(bbs, torch, h, dA, b, opts, reps=3):
+    """Best-of-reps CUDA-event time (ms) of one bbs_solve from x0 = 0, and the log."""
+    x = torch.zeros_like(b)
+    log = bbs.Log.empty(dA.num_batch, device=b.device)
+    ws = h.workspace(dA, opts)
+    h.solve(dA, b, x, opts, log, ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(reps):
+        x.zero_()
+        e0.record()
+        h.solve(dA, b, x, opts, log, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    st = log.status.cpu().numpy()
+    return best, float(log.iters.double().mean()), int((st == 0).sum())
+
+
+def pele_runs(bbs, torch, dev, num_batch=131072):
+    """The five PeleLM-shaped batches (BatchCsr, BiCGSTAB + scalar Jacobi, the
+    paper's Sec. 5.2 setup), each unique matrix repeated on the device."""
+    h = bbs.Handle(dev.index or 0)
+    out = {}
+    for mech, (U, n, nnz) in W.MECHANISMS.items():
+        wl = W.pele_like(mech, U)  # the unique matrices
+        uniq = torch.as_tensor(wl.csr_values, device=dev)
+        idx = torch.arange(num_batch, device=dev) % U
+        vals = uniq[idx].contiguous()
+        g = np.random.Generator(np.random.PCG64(W.SEED_BASE + 11))
+        b = torch.as_tensor(g.uniform(-1, 1, (num_batch, n)), device=dev)
+        res = {}
+        for fmt in ("csr", "dense"):
+            if fmt == "csr":
+                dA = bbs.DeviceBatch("csr", n, nnz, 0, torch.as_tensor(wl.pattern.row_ptrs, device=dev),
+                                     torch.as_tensor(wl.pattern.col_idxs, device=dev), vals)
+            else:
+                dense = torch.zeros(num_batch, n * n, dtype=torch.float64, device=dev)
+                rows = np.repeat(np.arange(n), np.diff(wl.pattern.row_ptrs))
+                pos = torch.as_tensor(rows * n + wl.pattern.col_idxs, device=dev)
+                dense[:, pos] = vals
+                dA = bbs.DeviceBatch("dense", n, nnz, 0, None, None, dense)
+            ms, it, conv = timed_solve(bbs, torch, h, dA, b, bbs.bbs_default_options())
+            per_it = 4 * (nnz if fmt == "csr" else n * n) + 26 * n
+            res[fmt] = {"ms": ms, "systems_per_s": num_batch / (ms / 1e3), "iters_mean": it,
+                        "converged": conv,
+                        "fp64_tflops": num_batch * it * (4 * nnz + 26 * n) / (ms / 1e3) / 1e12,
+                        "executed_tflops": num_batch * it * per_it / (ms / 1e3) / 1e12}
+            del dA
+        out[mech] = {"n": n, "nnz": nnz, "unique": U, "num_batch": num_batch, **res}
+        del vals, uniq
+        torch.cuda.empty_cache()
+    return out
+
+
+def sweep_runs(bbs, torch, dev):
+    """Scaling study of Sec. 5.1 on the 3-point SPD batch: matrix size at 2^17
+    systems and batch count at n = 64, for CG and BiCGSTAB (+ Jacobi)."""
+    h = bbs.Handle(dev.index or 0)
+    out = {"size": [], "batch": []}
+    for n in (16, 32, 64, 128, 256, 512, 1024):
+        wl = W.spd_tridiagonal(131072, n)
+        dA = bbs.DeviceBatch.from_batch(wl.matrix("csr"), dev)
+        b = torch.as_tensor(wl.b, device=dev)
+        for solver in ("cg", "bicgstab"):
+            ms, it, conv = timed_solve(bbs, torch, h, dA, b, bbs.bbs_default_options(solver=solver))
+            out["size"].append({"n": n, "solver": solver, "ms": ms, "iters_mean": it, "converged": conv,
+                                "systems_per_s": 131072 / (ms / 1e3)})
+        del dA, b, wl
+    wl = W.spd_tridiagonal(131072, 64)
+    for lb in range(13, 18):
+        B = 2 ** lb
+        A = wl.matrix("csr").subset(np.arange(B))
+        dA = bbs.DeviceBatch.from_batch(A, dev)
+        b = torch.as_tensor(wl.b[:B], device=dev)
+        for solver in ("cg", "bicgstab"):
+            ms, it, conv = timed_solve(bbs, torch, h, dA, b, bbs.bbs_default_options(solver=solver))
+            out["batch"].append({"num_batch": B, "solver": solver, "ms": ms, "iters_mean": it,
+                                 "converged": conv, "systems_per_s": B / (ms / 1e3)})
+    return out
+
+
 def learned_run(bbs, torch, dev, eval_steps=192, num_batch=16384):
     """Time-stepped batch: train on steps 0..63, then per step time (MLP
     prediction + solve) against (solve from x(t-1))."""
@@ -383,6 +466,15 @@ def extras(bbs, torch, dev, stream, mhz):
         del f64, mix
     except Exception as e:  # report, do not hide
         out["mixed"] = {"error": repr(e)}
+    try:  # the same headline batch with the batched ILU(0) preconditioner
+        il = Uniform(bbs, torch, dev, W.plain_at_scale(), "csr", dict(precond="ilu0"), "ilu0")
+        tot, ms, _ = time_steps(il, torch, stream, 5, 2)
+        out["ilu0"] = {"workload": il.wl.name, "value": il.num_batch * 5 / (tot / 1e3),
+                       "unit": "systems/s", "iterations": il.summary(),
+                       "note": "BiCGSTAB + ILU(0) (level-scheduled factorisation and triangular solves)"}
+        del il
+    except Exception as e:
+        out["ilu0"] = {"error": repr(e)}
     try:
         out["learned"] = learned_run(bbs, torch, dev, eval_steps=32)
     except Exception as e:
@@ -470,6 +562,13 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
+    if args.workload in ("pele", "sweep"):
+        res = pele_runs(bbs, torch, dev) if args.workload == "pele" else sweep_runs(bbs, torch, dev)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "workload": args.workload, "unit": "systems/s",
+                              "n_gpus": world, "dtype": "f64", "data": "synthetic", "results": res}),
+                  flush=True)
+        return
     if args.workload == "learned":
         s = learned_run(bbs, torch, dev, eval_steps=192, num_batch=args.systems or 16384)
         line = {"metric": METRIC, "value": s["systems_per_s_learned"], "unit": "systems/s",

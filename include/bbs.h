@@ -45,9 +45,14 @@ typedef enum { BBS_FMT_CSR = 0, BBS_FMT_ELL = 1, BBS_FMT_DENSE = 2 } bbs_format;
 /* Solvers, Table "Batched feature support": BatchBicgstab, BatchCg (Alg. 1),
  * BatchGmres (restarted). */
 typedef enum { BBS_SOLVER_BICGSTAB = 0, BBS_SOLVER_CG = 1, BBS_SOLVER_GMRES = 2 } bbs_solver;
-/* Preconditioners: none, or scalar BatchJacobi M = D^-1 (1 for a zero or
- * missing diagonal entry). */
-typedef enum { BBS_PREC_NONE = 0, BBS_PREC_JACOBI = 1 } bbs_precond;
+/* Preconditioners (Table "Batched feature support"): none; scalar
+ * BatchJacobi M = D^-1 (1 for a zero or missing diagonal entry); BatchIlu
+ * read as ILU(0): A ~ L U with unit lower L and upper U on A's pattern (zero
+ * fill-in, a zero pivot replaced by 1), applied by forward and backward
+ * triangular solves (BatchTrsv). ILU(0) preconditions FP64 BiCGSTAB on
+ * BatchCsr; the factors of a system must fit in shared memory (about 27,000
+ * nonzeros). */
+typedef enum { BBS_PREC_NONE = 0, BBS_PREC_JACOBI = 1, BBS_PREC_ILU0 = 2 } bbs_precond;
 /* Stopping criteria, Table "Batched feature support": stop when
  * ||b - A x||_2 <= tol (absolute) or <= tol * ||b||_2 (relative). */
 typedef enum { BBS_TOL_ABSOLUTE = 0, BBS_TOL_RELATIVE = 1 } bbs_tol_type;
@@ -131,7 +136,8 @@ bbs_status bbs_destroy(bbs_handle *handle);
 
 /* Bytes of DEVICE workspace bbs_solve needs for this problem (0 is possible).
  * Workspace use: the FP32 copy of the values in mixed mode when values_f32
- * is NULL, and the GMRES Krylov basis when it does not fit in shared memory. */
+ * is NULL, the GMRES Krylov basis when it does not fit in shared memory, and
+ * the ILU(0) level schedule of the shared pattern. */
 bbs_status bbs_workspace_size(const bbs_handle *handle, const bbs_batch_matrix *A,
                               const bbs_options *opts, size_t *bytes);
 

@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build
 
 SOLVERS = {"bicgstab": 0, "cg": 1, "gmres": 2}
-PRECONDS = {"none": 0, "jacobi": 1}
+PRECONDS = {"none": 0, "jacobi": 1, "ilu0": 2}
 TOL_TYPES = {"absolute": 0, "relative": 1}
 FORMATS = {"csr": 0, "ell": 1, "dense": 2}
 STATUS = {0: "converged", 1: "max_iter", 2: "breakdown", 3: "nan"}
@@ -44,6 +44,8 @@ def _configure(L):
                                    p_i64, p_i64, p_f64, p_f64, p_f64, ci, cd, ci, ci, p_i32,
                                    p_f64, p_i32, ci]
     L.om_solve_varsize.restype = None
+    L.om_ilu0_batch.argtypes = [ci, p_i32, p_i32, p_f64, ci, p_f64]
+    L.om_ilu0_batch.restype = None
     return L
 
 
@@ -99,6 +101,8 @@ def solve(fmt: str, n: int, nnz: int, ell_k: int, row_ptrs, col_idxs, values, b,
           solver="bicgstab", precond="jacobi", tol_type="relative", tol=1e-10,
           max_iters=500, restart=10, threads=0):
     """Solve every system; returns (x [B,n], iters, rel_res, status)."""
+    if precond == "ilu0" and (fmt != "csr" or solver == "cg"):
+        raise ValueError("ILU(0) preconditions BiCGSTAB and GMRES on BatchCsr")
     values = _f64(values)
     B = values.shape[0]
     b = _f64(b).reshape(B, n)
@@ -167,3 +171,14 @@ def solve_varsize(vb, *, solver="bicgstab", precond="jacobi", tol_type="relative
                            sp, voff, xoff, _f64(vb.values), _f64(vb.b), x, TOL_TYPES[tol_type],
                            float(tol), int(max_iters), int(restart), iters, rel, status, nt)
     return x, iters, rel, status
+
+
+def ilu0(row_ptrs, col_idxs, values):
+    """ILU(0) factors (unit L below the diagonal, U on and above) of every
+    system of a BatchCsr batch, in the pattern's layout."""
+    values = _f64(values)
+    B = values.shape[0]
+    rp, ci = _i32(row_ptrs), _i32(col_idxs)
+    lu = np.empty_like(values)
+    lib().om_ilu0_batch(len(rp) - 1, rp, ci, values, B, lu)
+    return lu

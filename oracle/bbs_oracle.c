@@ -26,6 +26,11 @@
  *                is monitored on its own (per-system iteration/residual log).
  *   Sec. 2.1     "precision format" as a parameter: the mixed mode runs the
  *                inner BiCGSTAB in FP32 inside an FP64 refinement loop.
+ *   Sec. 3, Table "Batched feature support": BatchIlu / BatchTrsv, read as
+ *                the incomplete LU factorisation with zero fill-in on the
+ *                shared CSR pattern (ILU(0), Saad's IKJ form) applied by a
+ *                forward (unit lower) and a backward (upper) triangular
+ *                solve; right preconditioner of BiCGSTAB and GMRES.
  *
  * Readings where the paper is silent (all shared with the CUDA path by
  * specification, not by code):
@@ -49,7 +54,7 @@
 
 enum { OM_CSR = 0, OM_ELL = 1, OM_DENSE = 2 };
 enum { OM_BICGSTAB = 0, OM_CG = 1, OM_GMRES = 2 };
-enum { OM_NOPRECOND = 0, OM_JACOBI = 1 };
+enum { OM_NOPRECOND = 0, OM_JACOBI = 1, OM_ILU0 = 2 };
 enum { OM_ABSOLUTE = 0, OM_RELATIVE = 1 };
 enum { OM_CONVERGED = 0, OM_MAX_ITER = 1, OM_BREAKDOWN = 2, OM_NAN = 3 };
 #define OM_MAX_RESTARTS 3
@@ -171,6 +176,104 @@ static void precond_setup(const om_mat *A, int precond, double *dinv)
     }
 }
 
+/* ILU(0) on the CSR pattern, in place in `lu` (a copy of A's values): for
+ * each row i, for each k < i stored in row i (ascending), a_ik /= a_kk and
+ * a_ij -= a_ik a_kj for every j > k stored in both rows i and k. The unit
+ * lower factor L and the upper factor U share the pattern. A zero pivot is
+ * replaced by 1 (the same rule as Jacobi's zero diagonal). */
+static void ilu0_factor(const om_mat *A, double *lu)
+{
+    const int n = A->n;
+    const int32_t *rp = A->row_ptrs, *ci = A->col_idxs;
+    for (int i = 0; i < n; ++i) {
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            const int k = ci[e];
+            if (k >= i)
+                break;
+            double pivot = 0.0; /* u_kk */
+            for (int f = rp[k]; f < rp[k + 1]; ++f)
+                if (ci[f] == k)
+                    pivot = lu[f];
+            if (pivot == 0.0)
+                pivot = 1.0;
+            lu[e] = lu[e] / pivot;
+            for (int g = e + 1; g < rp[i + 1]; ++g) { /* j = ci[g] > k */
+                const int j = ci[g];
+                for (int f = rp[k]; f < rp[k + 1]; ++f)
+                    if (ci[f] == j)
+                        lu[g] = lu[g] - lu[e] * lu[f];
+            }
+        }
+    }
+}
+
+/* z = U^-1 L^-1 v with the factors of ilu0_factor (L unit lower). */
+static void ilu0_apply(const om_mat *A, const double *lu, const double *v, double *z)
+{
+    const int n = A->n;
+    const int32_t *rp = A->row_ptrs, *ci = A->col_idxs;
+    for (int i = 0; i < n; ++i) { /* L y = v */
+        double sum = v[i];
+        for (int e = rp[i]; e < rp[i + 1]; ++e)
+            if (ci[e] < i)
+                sum = sum - lu[e] * z[ci[e]];
+        z[i] = sum;
+    }
+    for (int i = n - 1; i >= 0; --i) { /* U z = y */
+        double sum = z[i], d = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            if (ci[e] > i)
+                sum = sum - lu[e] * z[ci[e]];
+            else if (ci[e] == i)
+                d = lu[e];
+        }
+        z[i] = sum / (d != 0.0 ? d : 1.0);
+    }
+}
+
+/* The right preconditioner M^-1 of one system: Jacobi (dinv), none, or ILU(0). */
+typedef struct {
+    int kind;
+    const om_mat *A;
+    double *dinv; /* n: Jacobi / none */
+    double *lu;   /* nnz: ILU(0) factors */
+} om_prec;
+
+static int prec_init(om_prec *M, const om_mat *A, int kind)
+{
+    M->kind = kind;
+    M->A = A;
+    M->dinv = (double *)malloc(sizeof(double) * A->n);
+    M->lu = NULL;
+    if (kind == OM_ILU0) {
+        if (A->fmt != OM_CSR)
+            return 0;
+        const int nnz = A->row_ptrs[A->n];
+        M->lu = (double *)malloc(sizeof(double) * (nnz > 0 ? nnz : 1));
+        memcpy(M->lu, A->vals, sizeof(double) * nnz);
+        ilu0_factor(A, M->lu);
+    }
+    precond_setup(A, kind == OM_JACOBI ? OM_JACOBI : OM_NOPRECOND, M->dinv);
+    return 1;
+}
+
+static void prec_free(om_prec *M)
+{
+    free(M->dinv);
+    free(M->lu);
+}
+
+/* z = M^-1 v */
+static void prec_apply(const om_prec *M, const double *v, double *z)
+{
+    if (M->kind == OM_ILU0) {
+        ilu0_apply(M->A, M->lu, v, z);
+    } else {
+        for (int i = 0; i < M->A->n; ++i)
+            z[i] = M->dinv[i] * v[i];
+    }
+}
+
 static double dot(const double *a, const double *b, int n)
 {
     double sum = 0.0;
@@ -256,10 +359,11 @@ static void bicgstab(const om_mat *A, const double *b, double *x, const om_opts 
     if (start(A, b, x, o, res, &nb, &tau))
         return;
     double *buf = (double *)calloc((size_t)11 * n, sizeof(double));
-    double *dinv = buf, *r = buf + n, *rh = buf + 2 * n, *p = buf + 3 * n, *ph = buf + 4 * n;
+    double *r = buf + n, *rh = buf + 2 * n, *p = buf + 3 * n, *ph = buf + 4 * n;
     double *v = buf + 5 * n, *s = buf + 6 * n, *sh = buf + 7 * n, *t = buf + 8 * n;
     double *rt = buf + 9 * n, *tmp = buf + 10 * n;
-    precond_setup(A, o->precond, dinv);
+    om_prec M;
+    prec_init(&M, A, o->precond);
 
     residual(A, b, x, r, tmp);
     double rn = norm2(r, n);
@@ -289,8 +393,7 @@ static void bicgstab(const om_mat *A, const double *b, double *x, const om_opts 
         const double beta = (rho / rho_old) * (alpha / omega);
         for (int i = 0; i < n; ++i)
             p[i] = r[i] + beta * (p[i] - omega * v[i]);
-        for (int i = 0; i < n; ++i)
-            ph[i] = dinv[i] * p[i];
+        prec_apply(&M, p, ph);
         spmv(A, ph, v);
         const double sigma = dot(rh, v, n);
         if (!isfinite(sigma)) {
@@ -315,8 +418,7 @@ static void bicgstab(const om_mat *A, const double *b, double *x, const om_opts 
                 x[i] = x[i] + alpha * ph[i];
             candidate = 1;
         } else {
-            for (int i = 0; i < n; ++i)
-                sh[i] = dinv[i] * s[i];
+            prec_apply(&M, s, sh);
             spmv(A, sh, t);
             const double tt = dot(t, t, n);
             const double ts = dot(t, s, n);
@@ -371,6 +473,7 @@ static void bicgstab(const om_mat *A, const double *b, double *x, const om_opts 
     }
     finish(res, OM_MAX_ITER, o->max_iters, A, b, x, nb, rt, tmp);
 done:
+    prec_free(&M);
     free(buf);
 }
 
@@ -498,14 +601,15 @@ static void gmres(const om_mat *A, const double *b, double *x, const om_opts *o,
         return;
     double *buf = (double *)calloc((size_t)(m + 1) * n + 6 * (size_t)n, sizeof(double));
     double *V = buf;                         /* (m+1) x n, row j = basis vector j */
-    double *dinv = buf + (size_t)(m + 1) * n, *r = dinv + n, *w = r + n, *u = w + n;
+    double *r = buf + (size_t)(m + 1) * n + n, *w = r + n, *u = w + n;
     double *tmp = u + n, *zz = tmp + n;
     double *H = (double *)calloc((size_t)(m + 1) * m, sizeof(double)); /* H[i*m + j] */
     double *cs = (double *)calloc((size_t)m, sizeof(double));
     double *sn = (double *)calloc((size_t)m, sizeof(double));
     double *g = (double *)calloc((size_t)m + 1, sizeof(double));
     double *y = (double *)calloc((size_t)m, sizeof(double));
-    precond_setup(A, o->precond, dinv);
+    om_prec M;
+    prec_init(&M, A, o->precond);
 
     residual(A, b, x, r, tmp);
     double beta = norm2(r, n);
@@ -535,8 +639,7 @@ static void gmres(const om_mat *A, const double *b, double *x, const om_opts *o,
         for (int j = 0; j < m; ++j) {
             ++it;
             double *vj = V + (size_t)j * n;
-            for (int i = 0; i < n; ++i)
-                u[i] = dinv[i] * vj[i];
+            prec_apply(&M, vj, u);
             spmv(A, u, w);
             for (int i = 0; i <= j; ++i) { /* modified Gram-Schmidt */
                 const double *vi = V + (size_t)i * n;
@@ -596,8 +699,9 @@ static void gmres(const om_mat *A, const double *b, double *x, const om_opts *o,
                 sum = sum + y[i] * V[(size_t)i * n + l];
             zz[l] = sum;
         }
+        prec_apply(&M, zz, u);
         for (int l = 0; l < n; ++l)
-            x[l] = x[l] + dinv[l] * zz[l];
+            x[l] = x[l] + u[l];
         residual(A, b, x, r, tmp);
         beta = norm2(r, n);
         if (!isfinite(beta)) {
@@ -630,6 +734,7 @@ static void gmres(const om_mat *A, const double *b, double *x, const om_opts *o,
         }
     }
 done:
+    prec_free(&M);
     free(buf);
     free(H);
     free(cs);
@@ -785,6 +890,18 @@ void om_spmv_batch(int fmt, int n, int nnz, int ell_k, const int32_t *row_ptrs,
     for (int bi = 0; bi < num_batch; ++bi) {
         om_mat A = {fmt, n, ell_k, row_ptrs, col_idxs, values + vps * bi};
         spmv(&A, x + (size_t)n * bi, y + (size_t)n * bi);
+    }
+}
+
+/* ILU(0) factors of every system of a BatchCsr batch (test access). */
+void om_ilu0_batch(int n, const int32_t *row_ptrs, const int32_t *col_idxs, const double *values,
+                   int num_batch, double *lu)
+{
+    const int nnz = row_ptrs[n];
+    for (int bi = 0; bi < num_batch; ++bi) {
+        om_mat A = {OM_CSR, n, 0, row_ptrs, col_idxs, values + (size_t)nnz * bi};
+        memcpy(lu + (size_t)nnz * bi, A.vals, sizeof(double) * nnz);
+        ilu0_factor(&A, lu + (size_t)nnz * bi);
     }
 }
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(PKG, "libbbs.so")
 BBS_OK = 0
 FMT = {"csr": 0, "ell": 1, "dense": 2}
 SOLVER = {"bicgstab": 0, "cg": 1, "gmres": 2}
-PRECOND = {"none": 0, "jacobi": 1}
+PRECOND = {"none": 0, "jacobi": 1, "ilu0": 2}
 TOL = {"absolute": 0, "relative": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 SYS_STATUS = {0: "converged", 1: "max_iter", 2: "breakdown", 3: "nan"}

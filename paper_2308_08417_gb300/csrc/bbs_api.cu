@@ -69,7 +69,8 @@ struct Plan {
     size_t stage_off = 0;
     bool stage = false;
     bool gmres_ws = false;  // GMRES basis in the workspace
-    size_t ws_gmres = 0, ws_f32 = 0;
+    bool ilu = false;       // ILU(0): level schedule in the workspace, factors in shared memory
+    size_t ws_gmres = 0, ws_f32 = 0, ws_ilu = 0;
 };
 
 bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
@@ -89,7 +90,10 @@ bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
         return fail(BBS_ERR_INVALID_ARG, "dense n*n overflows int32");
     if (A->num_batch > 0 && A->values == nullptr) return fail(BBS_ERR_INVALID_ARG, "values is NULL");
     if (o->solver < 0 || o->solver > 2) return fail(BBS_ERR_INVALID_ARG, "unknown solver %d", o->solver);
-    if (o->precond < 0 || o->precond > 1) return fail(BBS_ERR_INVALID_ARG, "unknown preconditioner %d", o->precond);
+    if (o->precond < 0 || o->precond > 2) return fail(BBS_ERR_INVALID_ARG, "unknown preconditioner %d", o->precond);
+    if (o->precond == BBS_PREC_ILU0 &&
+        (A->fmt != BBS_FMT_CSR || o->solver != BBS_SOLVER_BICGSTAB || o->precision != BBS_PRECISION_FP64))
+        return fail(BBS_ERR_UNSUPPORTED, "ILU(0) preconditions FP64 BiCGSTAB on BatchCsr");
     if (o->tol_type < 0 || o->tol_type > 1) return fail(BBS_ERR_INVALID_ARG, "unknown tolerance type %d", o->tol_type);
     if (!(o->tol > 0.0)) return fail(BBS_ERR_INVALID_ARG, "tol must be > 0");
     if (o->max_iters < 0) return fail(BBS_ERR_INVALID_ARG, "max_iters must be >= 0");
@@ -147,6 +151,17 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
         }
     }
     base = align_up(base, 16);
+    if (o->precond == BBS_PREC_ILU0) {  // factors (nnz) and inverse U diagonal (n_pad) in shared memory
+        p->ilu = true;
+        p->stage = true;
+        p->stage_off = base;
+        p->smem = base + align_up(vps * 8, 16) + (size_t)p->n_pad * 8;
+        if (p->smem > (size_t)h->max_smem_optin)
+            return fail(BBS_ERR_UNSUPPORTED, "ILU(0) factors need %zu bytes of shared memory (max %d)", p->smem,
+                        h->max_smem_optin);
+        p->ws_ilu = align_up(bbs::ilu_workspace_bytes(n), 256);
+        return BBS_OK;
+    }
     const size_t stage_bytes = align_up(vps * (mixed ? 4 : 8), 16);
     const size_t limit = (size_t)h->max_smem_optin;
     bool stage = false;
@@ -162,7 +177,7 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
     return BBS_OK;
 }
 
-size_t workspace_bytes(const Plan& p) { return align_up(p.ws_gmres, 256) + p.ws_f32; }
+size_t workspace_bytes(const Plan& p) { return align_up(p.ws_gmres, 256) + p.ws_f32 + p.ws_ilu; }
 
 // BiCGSTAB with staged values and Jacobi runs the Jacobi-folded kernel.
 const void* pick_kernel(const bbs_options* o, int fmt, int R, bool staged) {
@@ -327,6 +342,17 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
         if ((e = bbs::launch_convert_f32(A->values, f32, P.vps * (size_t)A->num_batch, st)) != cudaSuccess)
             return cuda_fail(e, "FP32 conversion launch");
         P.values32 = f32;
+    }
+    if (p.ilu) {
+        int* sched = reinterpret_cast<int*>(ws);
+        if ((e = bbs::launch_ilu_analysis(A->n, A->row_ptrs, A->col_idxs, sched, st)) != cudaSuccess)
+            return cuda_fail(e, "ILU(0) analysis launch");
+        const void* fn = bbs::bicgstab_ilu_fn(p.R);
+        if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        const int* csched = sched;
+        void* args[] = {&P, &csched};
+        e = cudaLaunchKernel(fn, dim3((unsigned)A->num_batch), dim3((unsigned)p.threads), args, p.smem, st);
+        return e == cudaSuccess ? BBS_OK : cuda_fail(e, "ILU(0) solver launch");
     }
     const void* fn = pick_kernel(o, A->fmt, p.R, p.stage);
     if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");

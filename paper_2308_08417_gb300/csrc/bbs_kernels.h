@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstddef>
+#include <cstdint>
 #include <cuda_runtime.h>
 
 namespace bbs {
@@ -28,6 +29,10 @@ BBS_DECL(gmres)
 BBS_DECL(refine)
 #undef BBS_DECL
 
+const void* bicgstab_ilu_fn(int R);
+size_t ilu_workspace_bytes(int n);
+cudaError_t launch_ilu_analysis(int n, const int32_t* row_ptrs, const int32_t* col_idxs, int* ws,
+                                cudaStream_t stream);
 cudaError_t launch_convert_f32(const double* src, float* dst, size_t count, cudaStream_t stream);
 
 }  // namespace bbs

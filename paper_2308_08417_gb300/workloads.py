@@ -424,3 +424,80 @@ def time_stepped(num_batch: int = 16384, steps: int = 256, grid: int = 12) -> Ti
     noise = np.random.Generator(np.random.PCG64(SEED_BASE + 4 + 7919))
     Bn = stencil_values(pat, num_batch, noise, 0.05, 0.5)
     return TimeSeries(pat, A, Bn, b, c, steps)
+
+
+# --------------------------------------------------------------------------
+# PeleLM-shaped batches (Table "Reference for data inputs": n, nonzeros per
+# matrix, number of unique matrices; the matrices themselves are not
+# available, so random patterns of the same size and density stand in)
+# --------------------------------------------------------------------------
+
+MECHANISMS = {
+    # name: (unique matrices, n, nnz per matrix)
+    "drm19": (67, 22, 438),
+    "gri12": (73, 33, 978),
+    "gri30": (90, 54, 2560),
+    "dodecane_lu": (78, 54, 2332),
+    "isooctane": (72, 144, 6135),
+}
+
+
+def random_pattern(n: int, nnz: int, rng: np.random.Generator) -> Pattern:
+    """Full diagonal plus nnz - n off-diagonal entries at random positions,
+    placed in mirrored pairs (structurally symmetric, as reaction Jacobians of
+    a species set nearly are) with one unpaired entry when the count is odd."""
+    off = nnz - n
+    if off < 0 or off > n * (n - 1):
+        raise ValueError("nnz out of range")
+    pairs = [(i, j) for i in range(n) for j in range(i + 1, n)]
+    chosen = rng.choice(len(pairs), off // 2, replace=False)
+    entries = {(i, i) for i in range(n)}
+    for c in chosen:
+        i, j = pairs[c]
+        entries.add((i, j))
+        entries.add((j, i))
+    if off % 2:
+        free = [(j, i) for (i, j) in pairs if (j, i) not in entries]
+        entries.add(free[rng.integers(len(free))])
+    rows = [sorted(c for (r, c) in entries if r == i) for i in range(n)]
+    row_ptrs = np.zeros(n + 1, dtype=np.int32)
+    row_ptrs[1:] = np.cumsum([len(r) for r in rows])
+    col_idxs = np.array([c for r in rows for c in r], dtype=np.int32)
+    return Pattern(n, row_ptrs, col_idxs, "random")
+
+
+def general_values(pat: Pattern, count: int, rng: np.random.Generator, diag_lo: float,
+                   diag_hi: float) -> np.ndarray:
+    """Values [count, nnz]: every off-diagonal entry U[-1, 0] * (1 + U[-0.1, 0.1]),
+    diagonal = sum |off-diagonal| * (1 + U[lo, hi])."""
+    rows = np.repeat(np.arange(pat.n), np.diff(pat.row_ptrs))
+    diag = rows == pat.col_idxs
+    v = rng.uniform(-1.0, 0.0, (count, pat.nnz)) * (1.0 + rng.uniform(-0.1, 0.1, (count, pat.nnz)))
+    v[:, diag] = 0.0
+    offsum = np.add.reduceat(np.abs(v), pat.row_ptrs[:-1].astype(np.int64), axis=1)
+    v[:, diag] = offsum * (1.0 + rng.uniform(diag_lo, diag_hi, (count, pat.n)))
+    return v
+
+
+def pele_like(mechanism: str, num_batch: int = 131072) -> Workload:
+    """A batch of num_batch systems made of the mechanism's unique matrices
+    repeated in turn (system i uses matrix i mod U, as the paper replicates a
+    few cells' matrices to emulate a larger mesh); b ~ U[-1, 1] per system."""
+    U, n, nnz = MECHANISMS[mechanism]
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 5 + list(MECHANISMS).index(mechanism)))
+    pat = random_pattern(n, nnz, rng)
+    uniq = general_values(pat, U, rng, 0.05, 0.5)
+    vals = uniq[np.arange(num_batch) % U]
+    b = rng.uniform(-1.0, 1.0, (num_batch, n))
+    return Workload(f"{mechanism}_n{n}_nnz{nnz}_B{num_batch}", pat, vals, b, np.zeros_like(b),
+                    meta={"unique": U})
+
+
+def spd_tridiagonal(num_batch: int, n: int) -> Workload:
+    """The 3-point-stencil SPD batch of the scaling study (Sec. 5.1): symmetric
+    tridiagonal, strictly diagonally dominant, positive diagonal."""
+    rng = _rng(6)
+    pat = stencil_pattern("1d3", n)
+    vals = stencil_values(pat, num_batch, rng, 0.05, 0.5, symmetric=True)
+    b = rng.uniform(-1.0, 1.0, (num_batch, n))
+    return Workload(f"spd3pt_n{n}_B{num_batch}", pat, vals, b, np.zeros_like(b))

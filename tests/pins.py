@@ -273,3 +273,53 @@ def check_refine():
 
 
 ALL_CHECKS.append(check_refine)
+
+
+def _dense_lu_of(row_ptrs, col_idxs, lu_vals, n):
+    L = np.eye(n)
+    U = np.zeros((n, n))
+    for i in range(n):
+        for e in range(row_ptrs[i], row_ptrs[i + 1]):
+            j = col_idxs[e]
+            if j < i:
+                L[i, j] = lu_vals[e]
+            else:
+                U[i, j] = lu_vals[e]
+    return L, U
+
+
+def check_ilu():
+    """ILU(0): exact on a tridiagonal matrix (no fill-in exists), so the
+    preconditioned solvers finish in one iteration with the LU solution; on a
+    general pattern L U reproduces A on the pattern; solutions match LU."""
+    fails = []
+    wl = W.tiny_tridiagonal(16)
+    A = wl.matrix("csr")
+    D = W.to_dense(wl.pattern, wl.csr_values).reshape(-1, 32, 32)
+    xs = np.linalg.solve(D, wl.b[..., None])[..., 0]
+    for solver in ("bicgstab", "gmres"):
+        x, it, rel, st = oracle.solve_batch(A, wl.b, solver=solver, precond="ilu0", tol=1e-12)
+        if not (it == 1).all() or relerr(x, xs).max() > 1e-12 or not (st == 0).all():
+            fails.append(f"ILU tridiagonal {solver}: iters {np.unique(it)} err {relerr(x, xs).max():.2e}")
+    for wl in (W.plain_at_scale(8, grid=6), W.pele_like("drm19", 8)):
+        p = wl.pattern
+        lu = oracle.ilu0(p.row_ptrs, p.col_idxs, wl.csr_values)
+        Dn = W.to_dense(p, wl.csr_values).reshape(-1, p.n, p.n)
+        rows = np.repeat(np.arange(p.n), np.diff(p.row_ptrs))
+        for k in range(len(lu)):
+            L, U = _dense_lu_of(p.row_ptrs, p.col_idxs, lu[k], p.n)
+            prod = L @ U
+            e = np.abs(prod[rows, p.col_idxs] - Dn[k][rows, p.col_idxs]).max() / np.abs(Dn[k]).max()
+            if e > 1e-13:
+                fails.append(f"ILU pattern identity on {wl.name}: {e:.2e}")
+                break
+        xs = np.linalg.solve(Dn, wl.b[..., None])[..., 0]
+        for solver in ("bicgstab", "gmres"):
+            x, it, rel, st = oracle.solve_batch(wl.matrix("csr"), wl.b, solver=solver, precond="ilu0",
+                                                tol=1e-12)
+            if not (st == 0).all() or relerr(x, xs).max() > 1e-9:
+                fails.append(f"ILU {solver} on {wl.name}: err {relerr(x, xs).max():.2e}")
+    return fails
+
+
+ALL_CHECKS.append(check_ilu)

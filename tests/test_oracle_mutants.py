@@ -35,7 +35,12 @@ MUTANTS = [
     ("gmres_givens_sign", "H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;",
      "H[(i + 1) * m + j] = sn[i] * a + cs[i] * c;"),
     ("gmres_backsub_sign", "sum = sum - H[i * m + l] * y[l];", "sum = sum + H[i * m + l] * y[l];"),
-    ("gmres_update_no_precond", "x[l] = x[l] + dinv[l] * zz[l];", "x[l] = x[l] + zz[l];"),
+    ("gmres_update_no_precond", "x[l] = x[l] + u[l];", "x[l] = x[l] + zz[l];"),
+    ("ilu_no_pivot_division", "lu[e] = lu[e] / pivot;", "lu[e] = lu[e];"),
+    ("ilu_update_sign", "lu[g] = lu[g] - lu[e] * lu[f];", "lu[g] = lu[g] + lu[e] * lu[f];"),
+    ("ilu_forward_uses_upper", "            if (ci[e] < i)\n                sum = sum - lu[e] * z[ci[e]];",
+     "            if (ci[e] > i)\n                sum = sum - lu[e] * z[ci[e]];"),
+    ("ilu_backward_no_diagonal", "z[i] = sum / (d != 0.0 ? d : 1.0);", "z[i] = sum;"),
     ("gmres_mgs_index", "const double *vi = V + (size_t)i * n;", "const double *vi = V + (size_t)j * n;"),
     ("jacobi_not_inverted", "dinv[i] = (precond == OM_JACOBI && d != 0.0) ? 1.0 / d : 1.0;",
      "dinv[i] = (precond == OM_JACOBI && d != 0.0) ? d : 1.0;"),
