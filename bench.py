@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2308_08417_gb300 import workloads as W  # noqa: E402
+from paper_2308_08417_gb300.sharding import max_over_ranks  # noqa: E402
 
 METRIC = "systems solved/s to rel. residual 1e-10"
 
@@ -583,10 +584,7 @@ def main():
     r = make_runner(args.workload, bbs, torch, dev, args.systems)
     total_ms, solve_ms, clocks = time_steps(r, torch, stream, args.steps, args.warmup, dist,
                                             sample_clocks=True, dev_index=local)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)  # the job's time is its slowest rank's
     mhz = clocks.get("sm_mhz") or 2070.0
     value = r.num_batch * world * args.steps / (total_ms / 1e3)
     avg_solve_s = statistics.mean(solve_ms) / 1e3
