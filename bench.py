@@ -69,6 +69,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="uneven workload: default launch choices")
     return p.parse_args()
 
 
@@ -296,7 +297,7 @@ class Uneven:
                 f"every 10th system of {self.vb.name}, repeated to {done} solves")
 
 
-def make_runner(name, bbs, torch, dev, systems=0):
+def make_runner(name, bbs, torch, dev, systems=0, tune=True):
     if name == "mixed":
         wl = subset_workload(W.mixed_precision(), systems)
         # inner tolerance 1e-2: the fastest of 0.3 / 0.1 / 0.03 / 1e-2 / 1e-3 / 1e-4 in a sweep
@@ -306,7 +307,7 @@ def make_runner(name, bbs, torch, dev, systems=0):
         wl = subset_workload(W.mixed_precision(), systems)
         return Uniform(bbs, torch, dev, wl, "ell", dict(max_iters=2000), wl.name)
     if name == "uneven":
-        return Uneven(bbs, torch, dev, W.uneven(systems or 100000))
+        return Uneven(bbs, torch, dev, W.uneven(systems or 100000), tune=tune)
     wl = subset_workload(W.plain_at_scale(), systems)
     return Uniform(bbs, torch, dev, wl, "csr", {}, wl.name)
 
@@ -581,7 +582,7 @@ def main():
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
-    r = make_runner(args.workload, bbs, torch, dev, args.systems)
+    r = make_runner(args.workload, bbs, torch, dev, args.systems, tune=not args.no_tune)
     total_ms, solve_ms, clocks = time_steps(r, torch, stream, args.steps, args.warmup, dist,
                                             sample_clocks=True, dev_index=local)
     total_ms = max_over_ranks(total_ms, dist, dev)  # the job's time is its slowest rank's

@@ -347,16 +347,6 @@ bbs_status bbs_mlp_forward(bbs_mlp *mlp, const uint16_t *feats, int32_t M, float
 bbs_status bbs_mlp_predict(bbs_mlp *mlp, const bbs_batch_matrix *A, const double *b,
                            const double *x_prev, double *x0, void *stream);
 
-/* out[i] = a[i] * b[i] + c[i] rounded once (IEEE 754 fused multiply-add,
- * round to nearest even), evaluated with integer instructions only (FP64
- * arithmetic is scarce on GB300; the integer pipe is idle in the FP64
- * solvers). Equal to the hardware fma bit for bit: normal and zero operands
- * with normal results use the integer path, everything else the hardware
- * fma. DEVICE arrays of length n; asynchronous on stream. The paper has no
- * counterpart: this validates a building block of the FP64 kernels. */
-bbs_status bbs_fma64_int(const double *a, const double *b, const double *c, double *out, int64_t n,
-                         void *stream);
-
 /* Threads per system by the rule of Sec. 3.6: at least n, a multiple of the
  * warp size 32, at most `max_threads` (the device maximum, 1024 on GB300).
  * Returns 0 for n <= 0 or max_threads < 32. Host only. */

@@ -126,7 +126,6 @@ def lib():
         L.bbs_mlp_set_gemm.argtypes = [vp, i32]
         L.bbs_mlp_check.argtypes = [vp]
         L.bbs_gemm_bf16.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, i32, vp, i32]
-        L.bbs_fma64_int.argtypes = [vp, vp, vp, vp, C.c_int64, vp]
         L.bbs_paper_block_size.argtypes = [C.c_int32, C.c_int32]
         L.bbs_paper_block_size.restype = C.c_int32
         L.bbs_default_block_size.argtypes = [C.c_int32, C.c_int32]
@@ -140,7 +139,7 @@ def lib():
                      "bbs_mlp_set_params", "bbs_mlp_get_grads", "bbs_mlp_observe",
                      "bbs_mlp_finalize_stats", "bbs_mlp_make_samples", "bbs_mlp_gradients",
                      "bbs_mlp_train_step", "bbs_mlp_forward", "bbs_mlp_predict", "bbs_mlp_set_gemm",
-                     "bbs_mlp_check", "bbs_gemm_bf16", "bbs_fma64_int"):
+                     "bbs_mlp_check", "bbs_gemm_bf16"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -527,9 +526,3 @@ def bbs_gemm_bf16(handle: Handle, kind: str, A: torch.Tensor, B: torch.Tensor) -
                                _ptr(C_), N), "bbs_gemm_bf16")
     return C_
 
-
-def bbs_fma64_int(a: torch.Tensor, b: torch.Tensor, c: torch.Tensor) -> torch.Tensor:
-    """a*b + c (FP64, one rounding) computed on the integer pipe."""
-    out = torch.empty_like(a)
-    _check(lib().bbs_fma64_int(_ptr(a), _ptr(b), _ptr(c), _ptr(out), a.numel(), _stream(a)), "bbs_fma64_int")
-    return out
