@@ -49,11 +49,23 @@ FP32_FLOP_PER_CLK_SM = 256.0
 NUM_SMS = 152
 HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 
-# dram bytes (read + write) per launch of a kernel from an ncu capture of it,
-# scaled to the benchmark's launch; an entry is removed when its kernel changes.
-# bicgstab_folded_kernel: profiles/bicgstab_folded_kernel_stencil2d5_n144.md,
-# 280.8 MB for 32,768 systems -> 561.5 MB for the 65,536-system launch.
-TRAFFIC_BYTES = {"bicgstab_folded_kernel": 561.5e6}
+# dram bytes (read + write) of one launch of a kernel from an ncu capture of
+# it, with the number of systems that launch solved; the bench scales them to
+# its own launch by systems (traffic is the compulsory bytes, which grow in
+# proportion). An entry is removed when its kernel changes.
+#   bicgstab_folded_kernel: profiles/bicgstab_folded_kernel_stencil2d5_n144.md
+#   refine_kernel:          profiles/refine_kernel_stencil2d9_n1024.md
+#   varsize_kernel:         profiles/varsize_kernel_uneven_n16-1024.md
+TRAFFIC = {"bicgstab_folded_kernel": (280.8e6, 32768),
+           "refine_kernel": (545.0e6, 4096),
+           "varsize_kernel": (328.7e6, 20000)}
+
+
+def traffic_bytes(kernel, systems):
+    if kernel not in TRAFFIC:
+        return None
+    b, s = TRAFFIC[kernel]
+    return b / s * systems
 
 
 def parse():
@@ -443,7 +455,7 @@ def roofline(r, solve_ms, mhz):
     peak = per_clk * NUM_SMS * mhz * 1e6 / 1e12
     achieved = flops / avg_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get(r.kernel), "kernel": r.kernel,
+            "frac": achieved / peak, "traffic": traffic_bytes(r.kernel, r.num_batch), "kernel": r.kernel,
             "arith": arith,
             "peak_source": f"{arith.upper()} {per_clk:g} FLOP/clk/SM x {NUM_SMS} SMs x median SM clock {mhz:.0f} MHz"}
 
