@@ -76,6 +76,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="scale",
                    choices=["scale", "mixed", "uneven", "learned", "pele", "sweep"])
+    p.add_argument("--format", default="csr", choices=["csr", "ell", "dense"],
+                   help="batch format of the scale workload")
+    p.add_argument("--threads-per-system", type=int, default=0,
+                   help="launch shape of the scale workload (0: the library's choice)")
     p.add_argument("--systems", type=int, default=0,
                    help="solve only the first N systems of the workload (profiling runs)")
     p.add_argument("--no-e2e", action="store_true")
@@ -155,9 +159,10 @@ class Uniform:
         self.log = bbs.Log.empty(wl.num_batch, device=dev, inner=self.mixed)
         self.ws = self.h.workspace(self.dA, self.opts)
         self.num_batch = wl.num_batch
-        # BiCGSTAB + Jacobi with staged values runs the Jacobi-folded kernel
-        self.kernel = "refine_kernel" if self.mixed else "bicgstab_folded_kernel"
-        self.launches_per_step = 2 if (self.mixed and self.ws is not None) else 1
+        # the library's own account of the launch (kernel, shape, launches per solve)
+        self.launch = self.h.describe(self.dA, self.opts)
+        self.kernel = self.launch["kernel"]
+        self.launches_per_step = self.launch["launches"]
 
     def reset(self):
         self.x.copy_(self.x0)
@@ -309,7 +314,7 @@ class Uneven:
                 f"every 10th system of {self.vb.name}, repeated to {done} solves")
 
 
-def make_runner(name, bbs, torch, dev, systems=0, tune=True):
+def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0):
     if name == "mixed":
         wl = subset_workload(W.mixed_precision(), systems)
         # inner tolerance 1e-2: the fastest of 0.3 / 0.1 / 0.03 / 1e-2 / 1e-3 / 1e-4 in a sweep
@@ -321,7 +326,9 @@ def make_runner(name, bbs, torch, dev, systems=0, tune=True):
     if name == "uneven":
         return Uneven(bbs, torch, dev, W.uneven(systems or 100000), tune=tune)
     wl = subset_workload(W.plain_at_scale(), systems)
-    return Uniform(bbs, torch, dev, wl, "csr", {}, wl.name)
+    opts = {"threads_per_system": tps} if tps else {}
+    label = wl.name if fmt == "csr" else f"{wl.name}_{fmt}"
+    return Uniform(bbs, torch, dev, wl, fmt, opts, label)
 
 
 def timed_solve(bbs, torch, h, dA, b, opts, reps=3):
@@ -480,6 +487,16 @@ def extras(bbs, torch, dev, stream, mhz):
         del f64, mix
     except Exception as e:  # report, do not hide
         out["mixed"] = {"error": repr(e)}
+    try:  # the same headline batch with one system per warp (no packing)
+        ow = Uniform(bbs, torch, dev, W.plain_at_scale(), "csr", dict(threads_per_system=32),
+                     "one_system_per_warp")
+        tot, ms, _ = time_steps(ow, torch, stream, 5, 2)
+        out["one_system_per_warp"] = {"workload": ow.wl.name, "value": ow.num_batch * 5 / (tot / 1e3),
+                                      "unit": "systems/s", "launch": ow.launch, "iterations": ow.summary(),
+                                      "roofline": roofline(ow, ms, mhz)}
+        del ow
+    except Exception as e:
+        out["one_system_per_warp"] = {"error": repr(e)}
     try:  # the same headline batch with the batched ILU(0) preconditioner
         il = Uniform(bbs, torch, dev, W.plain_at_scale(), "csr", dict(precond="ilu0"), "ilu0")
         tot, ms, _ = time_steps(il, torch, stream, 5, 2)
@@ -594,7 +611,8 @@ def main():
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
-    r = make_runner(args.workload, bbs, torch, dev, args.systems, tune=not args.no_tune)
+    r = make_runner(args.workload, bbs, torch, dev, args.systems, tune=not args.no_tune, fmt=args.format,
+                    tps=args.threads_per_system)
     total_ms, solve_ms, clocks = time_steps(r, torch, stream, args.steps, args.warmup, dist,
                                             sample_clocks=True, dev_index=local)
     total_ms = max_over_ranks(total_ms, dist, dev)  # the job's time is its slowest rank's
@@ -609,6 +627,7 @@ def main():
             "config": {"workload": r.label, "num_batch_per_gpu": r.num_batch, "tol": 1e-10,
                        "solver": "bicgstab+jacobi", "l2": "inputs larger than L2 (no flush)"},
             "gpu_launches": args.steps * r.launches_per_step,
+            "launch": getattr(r, "launch", None),
             "clocks": clocks, "roofline": roofline(r, solve_ms, mhz),
             "iterations": r.summary(),
             "compulsory_hbm": {"bytes": hbm_bytes, "GB/s": hbm_bytes / avg_solve_s / 1e9,

@@ -81,7 +81,12 @@ typedef struct {
     int32_t num_batch;
     int32_t n;
     int32_t nnz;   /* CSR: pattern nonzeros; ELL/DENSE: informational */
-    int32_t ell_k; /* ELL width (max nonzeros per row); ignored otherwise */
+    int32_t ell_k; /* ELL: width (max nonzeros per row). CSR: 0, or the
+                      largest number of nonzeros in any row; with it, small
+                      systems can run packed several to a warp (their values
+                      staged in ELL order). A CSR row longer than a given
+                      ell_k makes every system of that call report
+                      BBS_SYS_NAN. DENSE: ignored. */
     const int32_t *row_ptrs;
     const int32_t *col_idxs;
     const double *values;
@@ -99,8 +104,15 @@ typedef struct {
     int32_t precision;     /* bbs_precision; mixed requires BiCGSTAB */
     double inner_tol;      /* mixed: relative tolerance of each inner solve, (0,1) */
     int32_t max_outer;     /* mixed: cap on refinement steps (>= 0) */
-    int32_t threads_per_system; /* 0: library choice; else a multiple of 32 in
-                                   [32, 1024] with ceil(n / threads) <= 8 */
+    int32_t threads_per_system; /* 0: library choice; 4, 8 or 16: packed
+                                   systems, 32 / threads of them per warp in
+                                   lockstep (FP64 BiCGSTAB or CG with Jacobi
+                                   or no preconditioner, staged values,
+                                   ceil(n / threads) <= 10); else a multiple
+                                   of 32 in [32, 1024] with
+                                   ceil(n / threads) <= 8. The library choice
+                                   packs systems of n <= 160 rows when enough
+                                   of them fit in an SM's shared memory. */
     int32_t values_in_smem;     /* 0: library choice, 1: stage each system's
                                    values in shared memory, -1: read them from
                                    global memory in every SpMV */
@@ -136,10 +148,35 @@ bbs_status bbs_destroy(bbs_handle *handle);
 
 /* Bytes of DEVICE workspace bbs_solve needs for this problem (0 is possible).
  * Workspace use: the FP32 copy of the values in mixed mode when values_f32
- * is NULL, the GMRES Krylov basis when it does not fit in shared memory, and
- * the ILU(0) level schedule of the shared pattern. */
+ * is NULL, the GMRES Krylov basis when it does not fit in shared memory, the
+ * ILU(0) level schedule of the shared pattern, and for packed systems on CSR
+ * the pattern as an ELL column table (2 * ell_k * n int32 + 256 bytes). */
 bbs_status bbs_workspace_size(const bbs_handle *handle, const bbs_batch_matrix *A,
                               const bbs_options *opts, size_t *bytes);
+
+/* The launch bbs_solve makes for (A, opts) on this handle's device (the
+ * multi-level dispatch of Sec. 3.3 made visible). Host-only: no GPU work,
+ * A's arrays are not read. `kernel` points at a static string naming the
+ * solver kernel: "bicgstab_packed_kernel", "cg_packed_kernel", "bicgstab_folded_kernel",
+ * "bicgstab_kernel", "bicgstab_ilu_kernel", "cg_kernel", "gmres_kernel" or
+ * "refine_kernel". threads_per_system is the lanes of one system (4, 8 or
+ * 16 when systems are packed 32 / lanes to a warp). launches counts every
+ * kernel of one bbs_solve (an FP32 conversion, an ILU(0) analysis or the
+ * CSR column table of packed systems runs before the solver kernel). Errors
+ * as bbs_solve's argument checks. */
+typedef struct bbs_launch_info {
+    const char *kernel;
+    int32_t grid;               /* blocks of the solver kernel */
+    int32_t block;              /* threads per block */
+    int32_t threads_per_system;
+    int32_t rows_per_thread;    /* R: rows each thread owns */
+    int64_t smem_bytes;         /* dynamic shared memory per block */
+    int32_t values_staged;      /* 1: the values are staged in shared memory */
+    int32_t launches;
+} bbs_launch_info;
+
+bbs_status bbs_describe(const bbs_handle *handle, const bbs_batch_matrix *A, const bbs_options *opts,
+                        bbs_launch_info *info);
 
 /* Solve every system of the batch (Sec. 3.2-3.4: one thread block per system,
  * one launch for the batch; Sec. 2.1: x holds the initial guess on entry and

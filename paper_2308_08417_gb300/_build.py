@@ -25,8 +25,21 @@ def nvcc() -> str:
     return cand
 
 
+# Translation units that take longest to compile start first.
+_SLOW_FIRST = ("bbs_varsize_k8", "bbs_varsize_k4", "bbs_k_bicgstab_", "bbs_k_gmres_", "bbs_k_cg_")
+
+
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+    def rank(path):
+        name = os.path.basename(path)
+        for i, key in enumerate(_SLOW_FIRST):
+            if name.startswith(key):
+                return i
+        return len(_SLOW_FIRST)
+
+    return sorted(srcs, key=rank)
 
 
 def _headers_mtime() -> float:

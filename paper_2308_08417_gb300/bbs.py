@@ -11,6 +11,7 @@ import ctypes as C
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 PKG = os.path.dirname(os.path.abspath(__file__))
@@ -43,6 +44,12 @@ class bbs_options(C.Structure):
 class bbs_log(C.Structure):
     _fields_ = [("iters", C.c_void_p), ("rel_res", C.c_void_p), ("status", C.c_void_p),
                 ("inner_iters", C.c_void_p)]
+
+
+class bbs_launch_info(C.Structure):
+    _fields_ = [("kernel", C.c_char_p), ("grid", C.c_int32), ("block", C.c_int32),
+                ("threads_per_system", C.c_int32), ("rows_per_thread", C.c_int32),
+                ("smem_bytes", C.c_int64), ("values_staged", C.c_int32), ("launches", C.c_int32)]
 
 
 class bbs_var_batch(C.Structure):
@@ -96,6 +103,7 @@ def lib():
         L.bbs_destroy.argtypes = [C.c_void_p]
         L.bbs_workspace_size.argtypes = [C.c_void_p, P(bbs_batch_matrix), P(bbs_options),
                                          P(C.c_size_t)]
+        L.bbs_describe.argtypes = [C.c_void_p, P(bbs_batch_matrix), P(bbs_options), P(bbs_launch_info)]
         L.bbs_solve.argtypes = [C.c_void_p, P(bbs_batch_matrix), C.c_void_p, C.c_void_p,
                                 P(bbs_options), P(bbs_log), C.c_void_p, C.c_size_t, C.c_void_p]
         L.bbs_solve_host.argtypes = [C.c_void_p, P(bbs_batch_matrix), C.c_void_p, C.c_void_p,
@@ -132,7 +140,7 @@ def lib():
         L.bbs_default_block_size.restype = C.c_int32
         L.bbs_last_error.restype = C.c_char_p
         L.bbs_version.restype = C.c_char_p
-        for name in ("bbs_default_options", "bbs_create", "bbs_destroy", "bbs_workspace_size",
+        for name in ("bbs_default_options", "bbs_create", "bbs_destroy", "bbs_workspace_size", "bbs_describe",
                      "bbs_solve", "bbs_solve_host", "bbs_solve_noalloc", "bbs_var_default_tuning",
                      "bbs_var_plan_create", "bbs_var_solve", "bbs_var_plan_destroy", "bbs_var_tune",
                      "bbs_mlp_create", "bbs_mlp_destroy", "bbs_mlp_param_count", "bbs_mlp_get_params",
@@ -220,7 +228,9 @@ class DeviceBatch:
         rp = t(A.row_ptrs, torch.int32) if A.fmt == "csr" else None
         ci = t(A.col_idxs, torch.int32) if A.fmt in ("csr", "ell") else None
         v32 = vals.to(torch.float32) if values_f32 else None
-        return cls(A.fmt, A.n, A.nnz, A.ell_k, rp, ci, vals, v32)
+        # CSR: pass the largest row length, which lets small systems run packed
+        k = int(np.diff(A.row_ptrs).max()) if A.fmt == "csr" and A.n > 0 else A.ell_k
+        return cls(A.fmt, A.n, A.nnz, k, rp, ci, vals, v32)
 
     def struct(self) -> bbs_batch_matrix:
         return bbs_batch_matrix(FMT[self.fmt], self.num_batch, self.n, self.nnz, self.ell_k,
@@ -273,6 +283,15 @@ class Handle:
         _check(lib().bbs_workspace_size(self._h, C.byref(s), C.byref(opts), C.byref(out)),
                "bbs_workspace_size")
         return int(out.value)
+
+    def describe(self, A: DeviceBatch, opts: bbs_options) -> dict:
+        """bbs_describe: the launch a solve of A with opts makes."""
+        info = bbs_launch_info()
+        s = A.struct()
+        _check(lib().bbs_describe(self._h, C.byref(s), C.byref(opts), C.byref(info)), "bbs_describe")
+        return {"kernel": info.kernel.decode(), "grid": info.grid, "block": info.block,
+                "threads_per_system": info.threads_per_system, "rows": info.rows_per_thread,
+                "smem": info.smem_bytes, "staged": bool(info.values_staged), "launches": info.launches}
 
     def workspace(self, A: DeviceBatch, opts: bbs_options) -> torch.Tensor | None:
         nb = self.workspace_size(A, opts)

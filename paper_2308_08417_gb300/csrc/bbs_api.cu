@@ -70,7 +70,10 @@ struct Plan {
     bool stage = false;
     bool gmres_ws = false;  // GMRES basis in the workspace
     bool ilu = false;       // ILU(0): level schedule in the workspace, factors in shared memory
+    int lanes = 32;         // < 32: packed kernel, 32 / lanes systems per one-warp block
+    size_t slice = 0;       // packed: shared-memory bytes per system
     size_t ws_gmres = 0, ws_f32 = 0, ws_ilu = 0;
+    size_t ws_tables = 0;   // packed CSR: ELL column table, value map and flag
 };
 
 bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
@@ -86,6 +89,8 @@ bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
         if ((long long)A->ell_k * A->n > 0x7fffffffLL)
             return fail(BBS_ERR_INVALID_ARG, "ELL ell_k*n overflows int32");
     }
+    if (A->fmt == BBS_FMT_CSR && A->ell_k < 0)
+        return fail(BBS_ERR_INVALID_ARG, "CSR ell_k must be 0 (unknown) or the largest row length");
     if (A->fmt == BBS_FMT_DENSE && (long long)A->n * A->n > 0x7fffffffLL)
         return fail(BBS_ERR_INVALID_ARG, "dense n*n overflows int32");
     if (A->num_batch > 0 && A->values == nullptr) return fail(BBS_ERR_INVALID_ARG, "values is NULL");
@@ -109,8 +114,16 @@ bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
             return fail(BBS_ERR_INVALID_ARG, "mixed mode needs max_outer >= 0 and max_iters >= 1");
     }
     const int t = o->threads_per_system;
-    if (t != 0 && (t < 32 || t > 1024 || (t % 32) != 0))
-        return fail(BBS_ERR_INVALID_ARG, "threads_per_system must be 0 or a multiple of 32 in [32, 1024]");
+    if (t == 4 || t == 8 || t == 16) {
+        if (o->solver == BBS_SOLVER_GMRES || o->precision != BBS_PRECISION_FP64 ||
+            o->precond == BBS_PREC_ILU0 || o->values_in_smem == -1)
+            return fail(BBS_ERR_UNSUPPORTED,
+                        "threads_per_system %d (packed systems) is provided for FP64 BiCGSTAB and CG "
+                        "with Jacobi or no preconditioner and staged values", t);
+    } else if (t != 0 && (t < 32 || t > 1024 || (t % 32) != 0)) {
+        return fail(BBS_ERR_INVALID_ARG,
+                    "threads_per_system must be 0, 4, 8, 16 or a multiple of 32 in [32, 1024]");
+    }
     if (o->values_in_smem < -1 || o->values_in_smem > 1)
         return fail(BBS_ERR_INVALID_ARG, "values_in_smem must be -1, 0 or 1");
     return BBS_OK;
@@ -118,10 +131,82 @@ bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
 
 int max_row_len(const bbs_batch_matrix* A) { return A->fmt == BBS_FMT_ELL ? A->ell_k : 0; }
 
+// Shared memory of a packed system: xa [n_pad] | xb [n_pad] | values. The
+// slice is padded to 8 L bytes past a multiple of 128, so the groups that
+// share a half-warp's shared-memory wavefront start on different banks.
+size_t packed_slice(int n_pad, size_t vps, int L, size_t* stage_off) {
+    *stage_off = align_up(2 * (size_t)n_pad * 8, 16);
+    const size_t raw = *stage_off + align_up(vps * 8, 16);
+    const size_t shift = (size_t)(8 * L) % 128;
+    return align_up(raw + 128 - shift, 128) - 128 + shift;
+}
+
+// Warps an SM keeps resident for a packed launch: one-warp blocks, limited by
+// the register cap of the kernel's launch bounds and by shared memory.
+int packed_warps_per_sm(size_t smem, int R) {
+    const size_t sm_bytes = 228 * 1024;  // per SM, with 1 KB reserved per block
+    const int by_smem = smem + 1024 > sm_bytes ? 0 : (int)(sm_bytes / (smem + 1024));
+    const int by_regs = R <= 5 ? 16 : 12;  // packed_min_blocks
+    return by_smem < by_regs ? by_smem : by_regs;
+}
+
+// The library's packing: the narrowest group of 4, 8 or 16 lanes that covers
+// n in at most kMaxPackedR rows per lane and still leaves kPackedMinWarps
+// warps resident per SM (narrower groups put more systems on each FP64
+// instruction; fewer warps leave the FP64 pipe idle). Measured on GB300
+// (BiCGSTAB + Jacobi, 32,768 systems): 22 rows, 438 values: 8 lanes (14
+// warps) 31.0 M systems/s, 4 lanes (7 warps) 28.5 M, one per warp 16.9 M;
+// 33 rows, 978 values (CSR): 16 lanes (13 warps) 13.4 M, 8 lanes (6 warps)
+// 12.7 M, one per warp 9.4 M; 54 rows, 2,560 values: 16 lanes (5 warps)
+// 5.1 M, one per warp 6.5 M.
+constexpr int kPackedMinWarps = 8;
+
 bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_options* o, Plan* p) {
     const int n = A->n;
+    const int tps = o->threads_per_system;
+    const bool packable = o->solver != BBS_SOLVER_GMRES && o->precision == BBS_PRECISION_FP64 &&
+                          o->precond != BBS_PREC_ILU0 && o->values_in_smem != -1;
+    // CSR packs through an ELL table of width ell_k (the caller's bound on
+    // the row length); the library packs it only while the padding stays
+    // small, and needs the bound in any case.
+    const bool csr = A->fmt == BBS_FMT_CSR;
+    const bool csr_ok = !csr || (A->ell_k > 0 && (size_t)A->ell_k * (size_t)n <= (size_t)A->nnz * 3 / 2);
+    if (packable && tps != 0 && csr && A->ell_k <= 0)
+        return fail(BBS_ERR_INVALID_ARG,
+                    "packed systems on CSR need ell_k = the largest number of nonzeros in a row");
+    if (packable && (tps == 4 || tps == 8 || tps == 16 || (tps == 0 && csr_ok))) {
+        const int n_pad = (n + 1) & ~1;
+        const size_t vps = csr ? (size_t)A->ell_k * (size_t)n : vals_per_system(A);
+        for (int L = tps ? tps : 4; L <= (tps ? tps : 16); L *= 2) {
+            const int R = (n + L - 1) / L;
+            size_t off = 0;
+            const size_t slice = packed_slice(n_pad, vps, L, &off);
+            const size_t smem = slice * (size_t)(32 / L);
+            if (tps != 0) {
+                if (R > bbs::kMaxPackedR)
+                    return fail(BBS_ERR_INVALID_ARG, "threads_per_system %d leaves %d rows per lane (max %d)",
+                                tps, R, bbs::kMaxPackedR);
+                if (smem > (size_t)h->max_smem_optin)
+                    return fail(BBS_ERR_UNSUPPORTED, "packed block needs %zu bytes of shared memory (max %d)",
+                                smem, h->max_smem_optin);
+            } else if (R > bbs::kMaxPackedR || smem > (size_t)h->max_smem_optin ||
+                       packed_warps_per_sm(smem, R) < kPackedMinWarps) {
+                continue;
+            }
+            p->lanes = L;
+            p->R = R;
+            p->threads = 32;
+            p->n_pad = n_pad;
+            p->stage = true;
+            p->stage_off = off;
+            p->slice = slice;
+            p->smem = smem;
+            if (csr) p->ws_tables = align_up(2 * vps * 4, 256) + 256;
+            return BBS_OK;
+        }
+    }
     const int rpt = o->precision == BBS_PRECISION_MIXED_IR ? kMixedRowsPerThread : kDefaultRowsPerThread;
-    p->threads = o->threads_per_system ? o->threads_per_system : bbs_default_block_size(n, rpt);
+    p->threads = tps ? tps : bbs_default_block_size(n, rpt);
     if (p->threads <= 0)
         return fail(BBS_ERR_UNSUPPORTED, "n = %d exceeds the largest supported system (%d rows)", n,
                     bbs::kMaxRows);
@@ -177,7 +262,9 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
     return BBS_OK;
 }
 
-size_t workspace_bytes(const Plan& p) { return align_up(p.ws_gmres, 256) + p.ws_f32 + p.ws_ilu; }
+size_t workspace_bytes(const Plan& p) {
+    return align_up(p.ws_gmres, 256) + p.ws_f32 + p.ws_ilu + p.ws_tables;
+}
 
 // BiCGSTAB with staged values and Jacobi runs the Jacobi-folded kernel.
 const void* pick_kernel(const bbs_options* o, int fmt, int R, bool staged) {
@@ -288,6 +375,37 @@ bbs_status bbs_workspace_size(const bbs_handle* h, const bbs_batch_matrix* A, co
     return BBS_OK;
 }
 
+bbs_status bbs_describe(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_options* o,
+                        bbs_launch_info* info) {
+    if (h == nullptr || info == nullptr) return fail(BBS_ERR_INVALID_ARG, "null handle or output");
+    bbs_status s = validate(A, o);
+    if (s != BBS_OK) return s;
+    Plan p;
+    if ((s = make_plan(h, A, o, &p)) != BBS_OK) return s;
+    std::memset(info, 0, sizeof *info);
+    const bool mixed = o->precision == BBS_PRECISION_MIXED_IR;
+    if (p.lanes < 32) {
+        info->kernel = o->solver == BBS_SOLVER_CG ? "cg_packed_kernel" : "bicgstab_packed_kernel";
+        info->grid = (A->num_batch + 32 / p.lanes - 1) / (32 / p.lanes);
+        info->threads_per_system = p.lanes;
+    } else {
+        info->kernel = p.ilu ? "bicgstab_ilu_kernel"
+                       : mixed ? "refine_kernel"
+                       : o->solver == BBS_SOLVER_CG ? "cg_kernel"
+                       : o->solver == BBS_SOLVER_GMRES ? "gmres_kernel"
+                       : (p.stage && o->precond == BBS_PREC_JACOBI) ? "bicgstab_folded_kernel"
+                                                                     : "bicgstab_kernel";
+        info->grid = A->num_batch;
+        info->threads_per_system = p.threads;
+    }
+    info->block = p.threads;
+    info->rows_per_thread = p.R;
+    info->smem_bytes = (int64_t)p.smem;
+    info->values_staged = p.stage ? 1 : 0;
+    info->launches = A->num_batch == 0 ? 0 : 1 + ((p.ws_f32 > 0 || p.ilu || p.ws_tables > 0) ? 1 : 0);
+    return BBS_OK;
+}
+
 bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, double* x,
                      const bbs_options* o, const bbs_log* log, void* workspace,
                      size_t ws_bytes, void* stream) {
@@ -353,6 +471,31 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
         void* args[] = {&P, &csched};
         e = cudaLaunchKernel(fn, dim3((unsigned)A->num_batch), dim3((unsigned)p.threads), args, p.smem, st);
         return e == cudaSuccess ? BBS_OK : cuda_fail(e, "ILU(0) solver launch");
+    }
+    if (p.lanes < 32) {
+        const int per_block = 32 / p.lanes;
+        P.slice = p.slice;
+        if (p.ws_tables > 0) {  // after the other workspace parts, 256-byte aligned
+            unsigned char* t = ws + (need - p.ws_tables);
+            const size_t cells = (size_t)A->ell_k * (size_t)A->n;
+            int32_t* xcols = reinterpret_cast<int32_t*>(t);
+            int32_t* xsrc = xcols + cells;
+            int32_t* flag = reinterpret_cast<int32_t*>(t + align_up(2 * cells * 4, 256));
+            if ((e = bbs::launch_csr_ell_tables(A->n, A->ell_k, A->row_ptrs, A->col_idxs, xcols, xsrc, flag, st)) !=
+                cudaSuccess)
+                return cuda_fail(e, "CSR table launch");
+            P.xcols = xcols;
+            P.xsrc = xsrc;
+            P.xflag = flag;
+            P.xk = A->ell_k;
+        }
+        const void* fn = o->solver == BBS_SOLVER_CG ? bbs::cg_packed_fn(A->fmt, p.lanes, p.R)
+                                                    : bbs::bicgstab_packed_fn(A->fmt, p.lanes, p.R);
+        if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        void* args[] = {&P};
+        const unsigned blocks = (unsigned)((A->num_batch + per_block - 1) / per_block);
+        e = cudaLaunchKernel(fn, dim3(blocks), dim3(32), args, p.smem, st);
+        return e == cudaSuccess ? BBS_OK : cuda_fail(e, "packed solver launch");
     }
     const void* fn = pick_kernel(o, A->fmt, p.R, p.stage);
     if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");

@@ -222,43 +222,53 @@ __device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(kFull
 template <typename T>
 __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(kFull, v, src); }
 
-template <typename T, int NV>
-__device__ __forceinline__ void warp_sum(T (&v)[NV], int lane) {
-    static_assert(NV >= 1 && NV <= 4, "warp_sum handles 1..4 values");
+// Sums of NV values over each aligned group of L lanes (L a power of two,
+// 4..32), returned to every lane of the group with identical bits. All 32
+// lanes of the warp must take part (every group runs the same instructions).
+template <int L, typename T, int NV>
+__device__ __forceinline__ void group_sum(T (&v)[NV], int lane) {
+    static_assert(NV >= 1 && NV <= 4, "group_sum handles 1..4 values");
+    static_assert(L >= 4 && L <= 32 && (L & (L - 1)) == 0, "L is a power of two in [4, 32]");
+    const int base = lane & ~(L - 1);
     if constexpr (NV == 1) {
         T a = v[0];
 #pragma unroll
-        for (int m = 16; m; m >>= 1) a += shfl_xor(a, m);
+        for (int m = L / 2; m; m >>= 1) a += shfl_xor(a, m);
         v[0] = a;
     } else if constexpr (NV == 2) {
-        const bool hi = lane & 16;
+        const bool hi = lane & (L / 2);
         T keep = hi ? v[1] : v[0];
         const T send = hi ? v[0] : v[1];
-        keep += shfl_xor(send, 16);
+        keep += shfl_xor(send, L / 2);
 #pragma unroll
-        for (int m = 8; m; m >>= 1) keep += shfl_xor(keep, m);
-        v[0] = shfl(keep, 0);
-        v[1] = shfl(keep, 16);
+        for (int m = L / 4; m; m >>= 1) keep += shfl_xor(keep, m);
+        v[0] = shfl(keep, base);
+        v[1] = shfl(keep, base + L / 2);
     } else {
         const T w3 = (NV == 4) ? v[NV - 1] : T(0);
-        const bool b4 = lane & 16;
+        const bool b4 = lane & (L / 2);
         T k0 = b4 ? v[2] : v[0];
         T k1 = b4 ? w3 : v[1];
         const T s0 = b4 ? v[0] : v[2];
         const T s1 = b4 ? v[1] : w3;
-        k0 += shfl_xor(s0, 16);
-        k1 += shfl_xor(s1, 16);
-        const bool b3 = lane & 8;
+        k0 += shfl_xor(s0, L / 2);
+        k1 += shfl_xor(s1, L / 2);
+        const bool b3 = lane & (L / 4);
         T keep = b3 ? k1 : k0;
         const T send = b3 ? k0 : k1;
-        keep += shfl_xor(send, 8);
+        keep += shfl_xor(send, L / 4);
 #pragma unroll
-        for (int m = 4; m; m >>= 1) keep += shfl_xor(keep, m);
-        v[0] = shfl(keep, 0);
-        v[1] = shfl(keep, 8);
-        v[2] = shfl(keep, 16);
-        if constexpr (NV == 4) v[3] = shfl(keep, 24);
+        for (int m = L / 8; m; m >>= 1) keep += shfl_xor(keep, m);
+        v[0] = shfl(keep, base);
+        v[1] = shfl(keep, base + L / 4);
+        v[2] = shfl(keep, base + L / 2);
+        if constexpr (NV == 4) v[3] = shfl(keep, base + 3 * L / 4);
     }
+}
+
+template <typename T, int NV>
+__device__ __forceinline__ void warp_sum(T (&v)[NV], int lane) {
+    group_sum<32, T, NV>(v, lane);
 }
 
 // red: shared scratch of 2 * 32 * 4 elements; parity alternates per call.

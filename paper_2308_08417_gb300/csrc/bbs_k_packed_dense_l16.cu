@@ -1,0 +1,18 @@
+// Packed BiCGSTAB and CG kernels (32 / L systems per warp), DENSE format,
+// L = 16 lanes per system, R = 1..kMaxPackedR rows per lane.
+#include "bbs_kernels.h"
+#include "bbs_packed.cuh"
+
+namespace bbs {
+#define BBS_TABLE(K)                                                                          \
+    static const void* const kTable[kMaxPackedR] = {                                         \
+        (const void*)K<FMT_DENSE, 16, 1>, (const void*)K<FMT_DENSE, 16, 2>, (const void*)K<FMT_DENSE, 16, 3>,   \
+        (const void*)K<FMT_DENSE, 16, 4>, (const void*)K<FMT_DENSE, 16, 5>, (const void*)K<FMT_DENSE, 16, 6>,   \
+        (const void*)K<FMT_DENSE, 16, 7>, (const void*)K<FMT_DENSE, 16, 8>, (const void*)K<FMT_DENSE, 16, 9>,   \
+        (const void*)K<FMT_DENSE, 16, 10>};                                                   \
+    return kTable[R - 1];
+static_assert(kMaxPackedR == 10, "tables cover R = 1..10");
+const void* bicgstab_packed_fn_dense_l16(int R) { BBS_TABLE(bicgstab_packed_kernel) }
+const void* cg_packed_fn_dense_l16(int R) { BBS_TABLE(cg_packed_kernel) }
+#undef BBS_TABLE
+}  // namespace bbs

@@ -32,6 +32,36 @@ cudaError_t launch_convert_f32(const double* src, float* dst, size_t count, cuda
     return cudaGetLastError();
 }
 
+// The CSR pattern as an ELL column table for the packed kernels: one thread
+// per row writes slot j of row r at j n + r (column, and the CSR index of the
+// value; -1 past the row's end). A row longer than k sets *flag and keeps
+// its first k entries.
+__global__ void csr_ell_tables_kernel(int n, int k, const int32_t* __restrict__ row_ptrs,
+                                      const int32_t* __restrict__ cols, int32_t* __restrict__ xcols,
+                                      int32_t* __restrict__ xsrc, int32_t* __restrict__ flag) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int e0 = row_ptrs[r];
+    int len = row_ptrs[r + 1] - e0;
+    if (len > k) {
+        atomicOr(flag, 1);
+        len = k;
+    }
+    for (int j = 0; j < k; ++j) {
+        const size_t i = (size_t)j * n + r;
+        xcols[i] = j < len ? cols[e0 + j] : -1;
+        xsrc[i] = j < len ? e0 + j : -1;
+    }
+}
+
+cudaError_t launch_csr_ell_tables(int n, int k, const int32_t* row_ptrs, const int32_t* cols, int32_t* xcols,
+                                  int32_t* xsrc, int32_t* flag, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int32_t), stream);
+    if (e != cudaSuccess) return e;
+    csr_ell_tables_kernel<<<(n + 127) / 128, 128, 0, stream>>>(n, k, row_ptrs, cols, xcols, xsrc, flag);
+    return cudaGetLastError();
+}
+
 #define BBS_FRONT(S)                                   \
     const void* S##_fn(int fmt, int R) {               \
         if (fmt == FMT_CSR) return S##_fn_csr(R);      \
@@ -43,5 +73,20 @@ BBS_FRONT(bicgstab_folded)
 BBS_FRONT(cg)
 BBS_FRONT(gmres)
 BBS_FRONT(refine)
+
+#define BBS_PACKED_FRONT(S)                                                                  \
+    const void* S##_packed_fn(int fmt, int L, int R) {                                       \
+        if (fmt == FMT_CSR)                                                                  \
+            return L == 4 ? S##_packed_fn_csr_l4(R) : L == 8 ? S##_packed_fn_csr_l8(R)       \
+                                                             : S##_packed_fn_csr_l16(R);     \
+        if (fmt == FMT_ELL)                                                                  \
+            return L == 4 ? S##_packed_fn_ell_l4(R) : L == 8 ? S##_packed_fn_ell_l8(R)       \
+                                                             : S##_packed_fn_ell_l16(R);     \
+        return L == 4 ? S##_packed_fn_dense_l4(R) : L == 8 ? S##_packed_fn_dense_l8(R)       \
+                                                           : S##_packed_fn_dense_l16(R);     \
+    }
+BBS_PACKED_FRONT(bicgstab)
+BBS_PACKED_FRONT(cg)
+#undef BBS_PACKED_FRONT
 
 }  // namespace bbs

@@ -29,6 +29,27 @@ BBS_DECL(gmres)
 BBS_DECL(refine)
 #undef BBS_DECL
 
+// Packed BiCGSTAB and CG (32 / L systems per warp): L = 4, 8 or 16 lanes
+// per system, R = 1..kMaxPackedR rows per lane.
+constexpr int kMaxPackedR = 10;
+#define BBS_DECL_PACKED(S)                       \
+    const void* S##_packed_fn(int fmt, int L, int R); \
+    const void* S##_packed_fn_csr_l4(int R);          \
+    const void* S##_packed_fn_csr_l8(int R);          \
+    const void* S##_packed_fn_csr_l16(int R);         \
+    const void* S##_packed_fn_ell_l4(int R);          \
+    const void* S##_packed_fn_ell_l8(int R);          \
+    const void* S##_packed_fn_ell_l16(int R);         \
+    const void* S##_packed_fn_dense_l4(int R);        \
+    const void* S##_packed_fn_dense_l8(int R);        \
+    const void* S##_packed_fn_dense_l16(int R);
+BBS_DECL_PACKED(bicgstab)
+BBS_DECL_PACKED(cg)
+#undef BBS_DECL_PACKED
+
+cudaError_t launch_csr_ell_tables(int n, int k, const int32_t* row_ptrs, const int32_t* cols, int32_t* xcols,
+                                  int32_t* xsrc, int32_t* flag, cudaStream_t stream);
+
 const void* bicgstab_ilu_fn(int R);
 size_t ilu_workspace_bytes(int n);
 cudaError_t launch_ilu_analysis(int n, const int32_t* row_ptrs, const int32_t* col_idxs, int* ws,

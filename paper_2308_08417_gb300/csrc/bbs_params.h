@@ -30,6 +30,14 @@ struct SolveParams {
     int stage;          // stage the system's values in shared memory
     size_t stage_off;   // byte offset of the staged values in dynamic shared memory
     double* ws;         // workspace (GMRES basis when it does not fit in shared memory)
+    size_t slice;       // packed kernels: shared-memory bytes per system
+    // packed kernels on CSR: the pattern as an ELL column table [xk * n]
+    // (column-major, -1 padding), the CSR index of each slot's value (-1
+    // padding), and a flag set when a row is longer than xk
+    const int32_t* xcols;
+    const int32_t* xsrc;
+    const int32_t* xflag;
+    int xk;
 };
 
 }  // namespace bbs

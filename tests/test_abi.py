@@ -79,3 +79,4 @@ def test_struct_layouts_match_header():
     assert bbs.bbs_options.tol.offset == 16 and bbs.bbs_options.inner_tol.offset == 32
     assert C.sizeof(bbs.bbs_batch_matrix) == 24 + 4 * 8
     assert C.sizeof(bbs.bbs_log) == 32
+    assert C.sizeof(bbs.bbs_launch_info) == 40 and bbs.bbs_launch_info.smem_bytes.offset == 24
