@@ -53,12 +53,12 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 # it, with the number of systems that launch solved; the bench scales them to
 # its own launch by systems (traffic is the compulsory bytes, which grow in
 # proportion). An entry is removed when its kernel changes.
+#   bicgstab_packed_kernel: profiles/bicgstab_packed_kernel_stencil2d5_n144.md
 #   bicgstab_folded_kernel: profiles/bicgstab_folded_kernel_stencil2d5_n144.md
 #   refine_kernel:          profiles/refine_kernel_stencil2d9_n1024.md
-#   varsize_kernel:         profiles/varsize_kernel_uneven_n16-1024.md
-TRAFFIC = {"bicgstab_folded_kernel": (280.8e6, 32768),
-           "refine_kernel": (545.0e6, 4096),
-           "varsize_kernel": (328.7e6, 20000)}
+TRAFFIC = {"bicgstab_packed_kernel": (135.8e6, 16384),
+           "bicgstab_folded_kernel": (280.8e6, 32768),
+           "refine_kernel": (545.0e6, 4096)}
 
 
 def traffic_bytes(kernel, systems):

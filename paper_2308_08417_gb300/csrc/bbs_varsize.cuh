@@ -58,16 +58,17 @@ struct VarParams {
 
 // Not inlined: each rows-per-thread variant is compiled as a function of its
 // own (one call per system), which keeps the persistent kernel's compile time
-// linear in the number of variants.
+// linear in the number of variants. Everything is passed by value, so that
+// the solver loops keep it in registers (a reference would leave it in the
+// caller's local memory).
 template <int R>
-__device__ __noinline__ void var_run(const VarParams& P, const Mat<double>& A, int nnz,
-                                        const SysIO& io, const TeamSmem& sm, double* stage,
-                                        const Team& tm) {
+__device__ __noinline__ void var_run(int solver, const SolveCfg cfg, const Mat<double> A, int nnz,
+                                     const SysIO io, const TeamSmem sm, double* stage, const Team tm) {
     const auto op = make_op<FMT_CSR, R>(A, (size_t)nnz, stage, tm);
-    if (P.solver == 1)
-        cg_system<FMT_CSR, R>(op, io, P.cfg, sm, tm);
+    if (solver == 1)
+        cg_system<FMT_CSR, R>(op, io, cfg, sm, tm);
     else
-        bicgstab_any<FMT_CSR, R>(op, io, P.cfg, sm, tm);
+        bicgstab_any<FMT_CSR, R>(op, io, cfg, sm, tm);
 }
 
 template <int R, int RMAX>
@@ -75,10 +76,10 @@ __device__ __forceinline__ void var_dispatch(int rows, const VarParams& P, const
                                              int nnz, const SysIO& io, const TeamSmem& sm,
                                              double* stage, const Team& tm) {
     if constexpr (R == RMAX) {
-        var_run<R>(P, A, nnz, io, sm, stage, tm);
+        var_run<R>(P.solver, P.cfg, A, nnz, io, sm, stage, tm);
     } else {
         if (rows <= R)
-            var_run<R>(P, A, nnz, io, sm, stage, tm);
+            var_run<R>(P.solver, P.cfg, A, nnz, io, sm, stage, tm);
         else
             var_dispatch<R + 1, RMAX>(rows, P, A, nnz, io, sm, stage, tm);
     }
@@ -108,7 +109,7 @@ __device__ __forceinline__ void var_solve_one(const VarParams& P, int sys, const
 }
 
 template <int RMAX>
-__global__ void __launch_bounds__(RMAX <= 4 ? 512 : 256, 1) varsize_kernel(const VarParams P) {
+__global__ void __launch_bounds__(RMAX <= 4 ? 512 : 256, 1) varsize_kernel(const __grid_constant__ VarParams P) {
     extern __shared__ __align__(16) unsigned char raw[];
     const int warp = threadIdx.x >> 5;
     for (int seg = 0; seg < P.num_segments; ++seg) {
