@@ -25,8 +25,10 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include "../../include/bbs.h"
 #include "bbs_internal.h"
@@ -57,6 +59,7 @@ struct Epi {
     int mode;
     float* c;                 // EPI_F32 / EPI_BIAS: output; EPI_BIAS_GELU: pre-activation store
     int ldc;
+    size_t zstride;           // EPI_F32: split-K part blockIdx.z goes to c + blockIdx.z * zstride
     const float* bias;        // EPI_BIAS_GELU / EPI_BIAS
     __nv_bfloat16* y;         // BF16 row-major output (EPI_BIAS_GELU, EPI_GELU_BWD)
     int ldy;
@@ -68,7 +71,7 @@ struct Epi {
     __device__ __forceinline__ void operator()(int m, int n, float v) const {
         switch (mode) {
             case EPI_F32:
-                c[(size_t)m * ldc + n] = v;
+                c[(size_t)blockIdx.z * zstride + (size_t)m * ldc + n] = v;
                 break;
             case EPI_BIAS:
                 c[(size_t)m * ldc + n] = v + bias[n];
@@ -97,10 +100,22 @@ __global__ void __launch_bounds__(256) gemm_kernel(const __nv_bfloat16* __restri
     gemm_tn_mma<Epi>(A, lda, B, ldb, M, N, K, epi);
 }
 
-__global__ void __launch_bounds__(128, 1) gemm_umma_kernel(const __nv_bfloat16* __restrict__ A, int lda,
-                                                           const __nv_bfloat16* __restrict__ B, int ldb,
-                                                           int M, int N, int K, int BN, Epi epi, int* err) {
-    umma::gemm_tn_umma<Epi>(A, lda, B, ldb, M, N, K, BN, epi, err);
+__global__ void __launch_bounds__(128, 1) gemm_umma_kernel(const __grid_constant__ CUtensorMap ta,
+                                                           const __grid_constant__ CUtensorMap tb, int M, int N,
+                                                           int K, int BN, int ktiles_per_split, Epi epi,
+                                                           int* err) {
+    umma::gemm_tn_tma<Epi>(&ta, &tb, M, N, K, BN, ktiles_per_split, epi, err);
+}
+
+// c[m][n] = sum over the splits of part[z][m][n] (split-K, fixed order).
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ part, float* __restrict__ c,
+                                     int ldc) {
+    const size_t total = (size_t)M * N;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * total + i];
+        c[(i / N) * ldc + i % N] = s;
+    }
 }
 
 // ---------------------------------------------------- small kernels
@@ -327,6 +342,9 @@ struct bbs_mlp {
     __nv_bfloat16* DZT[3] = {};
     int32_t* idx = nullptr;
     int* err = nullptr;     // set by a tensor-core GEMM whose waits ran out
+    float* part = nullptr;  // split-K partial sums of the weight-gradient GEMMs
+    size_t part_cap = 0;    // floats
+    int sms = 0;
     int gemm_kind = BBS_GEMM_TCGEN05;  // or BBS_GEMM_MMA_SYNC
     std::vector<void*> allocs;
 };
@@ -354,23 +372,87 @@ bool dev_alloc(bbs_mlp* m, T** ptr, size_t count) {
     return true;
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime (no -lcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// TMA map of a K-major BF16 operand [rows, K] (row stride ld elements) read
+// in boxes of 8 K-elements (16 bytes) by box_rows rows; rows past the end
+// read as zeros.
+bool make_operand_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int K, int ld, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (enc == nullptr) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // C = A B^T through the chosen tensor-core path (kind 1: tcgen05 with the
 // accumulator in tensor memory, K a multiple of 64; kind 0: mma.sync).
+// tcgen05 tiles: 128 rows x BN columns, BN <= 64 so that the layer GEMMs
+// over thousands of samples launch hundreds of blocks. An FP32-output GEMM
+// with few tiles and a long K (the weight gradients, K = samples) is split
+// over K when `part` has room: each split writes its partial tile, and
+// splitk_reduce_kernel adds them in a fixed order.
 cudaError_t gemm_any(int kind, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
-                     int K, const Epi& e, int* err, cudaStream_t st) {
+                     int K, const Epi& e, int* err, cudaStream_t st, float* part = nullptr, size_t part_cap = 0,
+                     int sms = 152) {
     if (kind == BBS_GEMM_TCGEN05) {
-        const int BN = std::min(256, round_up(N, 16));
+        const int ntile = (N + 63) / 64;
+        const int BN = std::max(16, round_up((N + ntile - 1) / ntile, 16));
+        const int mt = (M + bbs::umma::kBM - 1) / bbs::umma::kBM, nt = (N + BN - 1) / BN;
+        const int nk = K / bbs::umma::kBK;
+        int splits = 1, kps = nk;
+        const int want = 2 * sms;  // two blocks per SM fit (96 KB of stages each)
+        if (e.mode == bbs::mlp::EPI_F32 && part != nullptr && mt * nt < want && nk >= 8) {
+            splits = std::min((want + mt * nt - 1) / (mt * nt), nk / 4);
+            while (splits > 1 && (size_t)splits * M * N > part_cap) --splits;
+            if (splits > 1) {
+                kps = (nk + splits - 1) / splits;
+                splits = (nk + kps - 1) / kps;  // every split has k-tiles
+            }
+        }
+        CUtensorMap ta, tb;
+        if (!make_operand_map(&ta, A, M, K, lda, bbs::umma::kBM) || !make_operand_map(&tb, B, N, K, ldb, BN))
+            return cudaErrorInvalidValue;
         const size_t smem = bbs::umma::smem_bytes(BN);
         static bool attr_set = false;
         if (!attr_set) {
             cudaError_t a = cudaFuncSetAttribute(bbs::mlp::gemm_umma_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)bbs::umma::smem_bytes(256));
+                                                 (int)bbs::umma::smem_bytes(64));
             if (a != cudaSuccess) return a;
             attr_set = true;
         }
-        dim3 grid((N + BN - 1) / BN, (M + bbs::umma::kBM - 1) / bbs::umma::kBM);
-        bbs::mlp::gemm_umma_kernel<<<grid, 128, smem, st>>>(A, lda, B, ldb, M, N, K, BN, e, err);
+        dim3 grid(nt, mt, splits);
+        if (splits == 1) {
+            bbs::mlp::gemm_umma_kernel<<<grid, 128, smem, st>>>(ta, tb, M, N, K, BN, kps, e, err);
+            return cudaGetLastError();
+        }
+        Epi pe = e;
+        pe.c = part;
+        pe.ldc = N;
+        pe.zstride = (size_t)M * N;
+        bbs::mlp::gemm_umma_kernel<<<grid, 128, smem, st>>>(ta, tb, M, N, K, BN, kps, pe, err);
+        const size_t total = (size_t)M * N;
+        const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)sms * 8);
+        bbs::mlp::splitk_reduce_kernel<<<blocks, 256, 0, st>>>(M, N, splits, part, e.c, e.ldc);
         return cudaGetLastError();
     }
     dim3 grid((N + bbs::mlp::kBN - 1) / bbs::mlp::kBN, (M + bbs::mlp::kBM - 1) / bbs::mlp::kBM);
@@ -380,7 +462,7 @@ cudaError_t gemm_any(int kind, const __nv_bfloat16* A, int lda, const __nv_bfloa
 
 cudaError_t gemm(bbs_mlp* m, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
                  int K, const Epi& e, cudaStream_t st) {
-    return gemm_any(m->gemm_kind, A, lda, B, ldb, M, N, K, e, m->err, st);
+    return gemm_any(m->gemm_kind, A, lda, B, ldb, M, N, K, e, m->err, st, m->part, m->part_cap, m->sms);
 }
 
 Epi epi_f32(float* c, int ldc) {
@@ -513,6 +595,13 @@ bbs_status bbs_mlp_create(bbs_handle* h, int32_t n, int32_t hidden, uint64_t see
         ok = dev_alloc(m, &m->Z[l], MB * hidden) && dev_alloc(m, &m->Y[l], MB * hidden) &&
              dev_alloc(m, &m->YT[l], MB * hidden) && dev_alloc(m, &m->DZ[l], MB * hidden) &&
              dev_alloc(m, &m->DZT[l], MB * hidden);
+    // split-K partials of the weight gradients: up to 32 splits of the largest [out, in]
+    size_t wmax = 0;
+    for (int l = 0; l < 4; ++l) wmax = std::max(wmax, (size_t)outs[l] * ins[l]);
+    m->part_cap = 32 * wmax;
+    ok = ok && dev_alloc(m, &m->part, m->part_cap);
+    cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
+    if (m->sms <= 0) m->sms = 152;
     if (!ok) {
         bbs_mlp_destroy(m);
         return errf(BBS_ERR_NO_MEMORY, "MLP buffers");
@@ -677,12 +766,18 @@ bbs_status bbs_gemm_bf16(bbs_handle* h, int32_t kind, const uint16_t* A, int32_t
         cudaFree(err);
         return errf(BBS_ERR_INVALID_ARG, "K must be positive");
     }
+    float* part = nullptr;
+    const size_t part_cap = (size_t)32 * M * N;
+    if (kind == BBS_GEMM_TCGEN05 && cudaMalloc(&part, part_cap * sizeof(float)) != cudaSuccess) part = nullptr;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, bbs::handle_device(h));
     e = gemm_any(kind, reinterpret_cast<const __nv_bfloat16*>(A), lda, reinterpret_cast<const __nv_bfloat16*>(B),
-                 ldb, M, N, K, ep, err, nullptr);
+                 ldb, M, N, K, ep, err, nullptr, part, part ? part_cap : 0, sms > 0 ? sms : 152);
     int flag = 0;
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(err);
+    if (part) cudaFree(part);
     if (e != cudaSuccess) return errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
     return flag ? errf(BBS_ERR_CUDA, "the tensor-core GEMM gave up waiting for its MMAs") : BBS_OK;
 }

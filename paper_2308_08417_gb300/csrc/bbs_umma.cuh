@@ -1,32 +1,39 @@
 // BF16 GEMM on the 5th-generation tensor cores (tcgen05) with the FP32
-// accumulator in tensor memory:
+// accumulator in tensor memory and TMA-fed shared-memory stages:
 //   C[m][n] = sum_k A[m*lda + k] * B[n*ldb + k]     (both operands K-major)
 // K must be a multiple of 64 and the row strides multiples of 8 elements.
 //
-// One block of 4 warps computes a 128 x BN tile (BN a multiple of 16, <= 256):
-//   * all threads stage 128x64 A and BNx64 B k-tiles into shared memory with
-//     cp.async, two stages, in the no-swizzle K-major "core matrix" layout
-//     (8 rows x 16 bytes per 128-byte core matrix; core matrices adjacent in
-//     K are 128 bytes apart, 8-row groups 1024 bytes apart);
-//   * thread 0 issues four tcgen05.mma (M=128, N=BN, K=16 each) per k-tile
-//     and commits them to the stage's mbarrier, which frees the stage;
-//   * after the last commit every warp reads its 32 accumulator lanes (rows)
-//     with tcgen05.ld and runs the epilogue functor epi(m, n, value).
-// Every mbarrier wait is bounded; a wait that runs out sets *err, skips the
-// remaining work and still releases the tensor memory.
+// One block of 4 warps computes a 128 x BN tile (BN a multiple of 16, <= 256)
+// over the k-tiles [kt0, kt1) of its split (blockIdx.z):
+//   * thread 0 of warp 0 is the producer: for each 64-wide k-tile it issues
+//     TMA copies (cp.async.bulk.tensor.2d) of eight 16-byte-wide column boxes
+//     of A (128 rows) and of B (BN rows) into one of kStages stages, laid out
+//     as the no-swizzle K-major "core matrix" canonical form (8 rows x 16
+//     bytes per 128-byte core matrix; 8-row groups 128 bytes apart, 16-byte
+//     K chunks 16 * rows bytes apart), and arms the stage's "full" mbarrier
+//     with the byte count;
+//   * thread 0 of warp 1 issues four tcgen05.mma (M = 128, N = BN, K = 16)
+//     per k-tile once the stage is full, and tcgen05.commit frees the stage
+//     through its "empty" mbarrier; a last commit signals "done";
+//   * then every warp reads its 32 accumulator lanes (rows) with tcgen05.ld
+//     and runs the epilogue functor epi(m, n, value).
+// Rows past M and N are zero-filled by TMA. Every mbarrier wait is bounded;
+// a wait that runs out sets *err, the block stops issuing, waits (bounded)
+// for the copies and MMAs it already issued, and still frees its tensor
+// memory.
 #pragma once
 
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-
-#include "bbs_mlp_gemm.cuh"
 
 namespace bbs {
 namespace umma {
 
-constexpr int kBM = 128, kBK = 64;
+constexpr int kBM = 128, kBK = 64, kStages = 4;
+constexpr int kWaitIters = 1 << 22;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -47,14 +54,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Byte offset of 16-byte chunk `kc` (8 elements along K) of row `r` in a
-// tile stored as 8-row groups of core matrices, 8 chunks per row (K = 64).
-__device__ __forceinline__ uint32_t core_off(int r, int kc) {
-    return (uint32_t)((((r >> 3) * 8 + kc) << 7) + ((r & 7) << 4));
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 22); ++i) {
+    for (int i = 0; i < kWaitIters; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -65,6 +74,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         if (done) return true;
     }
     return false;
+}
+
+// 2D tiled TMA load of box (x = K element offset, y = row) into shared memory,
+// completing on mbarrier `bar` (byte count armed by mbar_expect_tx).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -91,23 +110,33 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
-// Dynamic shared memory the kernel needs for a BN-wide tile.
-__host__ __device__ constexpr size_t smem_bytes(int BN) {
-    return 2 * ((size_t)kBM * kBK * 2 + (size_t)BN * kBK * 2) + 64;
-}
+// Dynamic shared memory of a BN-wide tile: kStages stages of A and B, then
+// the barriers (full[kStages], empty[kStages], done) and the TMEM slot.
+__host__ __device__ constexpr size_t stage_bytes(int BN) { return (size_t)kBM * kBK * 2 + (size_t)BN * kBK * 2; }
+__host__ __device__ constexpr size_t smem_bytes(int BN) { return kStages * stage_bytes(BN) + 128 + 1024; }
 
 template <class Epi>
-__device__ __forceinline__ void gemm_tn_umma(const __nv_bfloat16* __restrict__ A, int lda,
-                                             const __nv_bfloat16* __restrict__ B, int ldb, int M, int N,
-                                             int K, int BN, const Epi& epi, int* err) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+__device__ __forceinline__ void gemm_tn_tma(const CUtensorMap* ta, const CUtensorMap* tb, int M, int N, int K,
+                                            int BN, int ktiles_per_split, const Epi& epi, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    // TMA destinations and MMA operands: 1024-byte aligned base
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+    const int nk = K / kBK;
+    const int kt0 = blockIdx.z * ktiles_per_split;
+    const int kt1 = min(nk, kt0 + ktiles_per_split);
     const uint32_t a_bytes = kBM * kBK * 2, b_bytes = (uint32_t)BN * kBK * 2;
-    const uint32_t stage_bytes = a_bytes + b_bytes;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const uint32_t sbytes = a_bytes + b_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * sbytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kStages;
+    uint64_t* done = bars + 2 * kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     const uint32_t tmem_cols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
+    // K-major no-swizzle layout written by the column boxes
+    const uint32_t lbo_a = kBM * 16, lbo_b = (uint32_t)BN * 16, sbo = 128;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
@@ -115,9 +144,12 @@ __device__ __forceinline__ void gemm_tn_umma(const __nv_bfloat16* __restrict__ A
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&mbar[1])) : "memory");
+    if (tid == 32) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(saddr(&full[s]), 1);
+            mbar_init(saddr(&empty[s]), 1);
+        }
+        mbar_init(saddr(done), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -125,57 +157,52 @@ __device__ __forceinline__ void gemm_tn_umma(const __nv_bfloat16* __restrict__ A
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = idesc_bf16(kBM, BN);
-
-    auto load = [&](int s, int kt) {
-        unsigned char* a = smem + s * stage_bytes;
-        unsigned char* b = a + a_bytes;
-        const int k0 = kt * kBK;
-        for (int c = tid; c < kBM * 8; c += 128) {
-            const int r = c >> 3, kc = c & 7, gm = m0 + r;
-            mlp::cp_async16(a + core_off(r, kc), A + (size_t)(gm < M ? gm : 0) * lda + k0 + kc * 8, gm < M ? 16 : 0);
-        }
-        for (int c = tid; c < BN * 8; c += 128) {
-            const int r = c >> 3, kc = c & 7, gn = n0 + r;
-            mlp::cp_async16(b + core_off(r, kc), B + (size_t)(gn < N ? gn : 0) * ldb + k0 + kc * 8, gn < N ? 16 : 0);
-        }
-        mlp::cp_async_commit();
-    };
-
-    const int nk = K / kBK;
-    uint32_t phase[2] = {0u, 0u};
+    const uint32_t base = saddr(smem);
     bool ok = true;
-    load(0, 0);
-    for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt & 1;
-        if (kt + 1 < nk) {
-            if (kt >= 1) {  // the other stage is free once the MMAs of k-tile kt-1 completed
-                ok = ok && mbar_wait(saddr(&mbar[s ^ 1]), phase[s ^ 1]);
-                phase[s ^ 1] ^= 1u;
+
+    if (tid == 0) {  // producer
+        int issued = 0;
+        for (int kt = kt0; kt < kt1; ++kt, ++issued) {
+            const int s = issued % kStages;
+            if (issued >= kStages && !mbar_wait(saddr(&empty[s]), ((issued / kStages) - 1) & 1)) {
+                ok = false;
+                break;
             }
-            load(s ^ 1, kt + 1);
-            mlp::cp_async_wait<1>();
-        } else {
-            mlp::cp_async_wait<0>();
+            const uint32_t a = base + s * sbytes, b = a + a_bytes, fb = saddr(&full[s]);
+            mbar_expect_tx(fb, sbytes);
+            const int k0 = kt * kBK;
+#pragma unroll
+            for (int kc = 0; kc < kBK / 8; ++kc) {
+                tma_load_2d(a + kc * lbo_a, ta, k0 + 8 * kc, m0, fb);
+                tma_load_2d(b + kc * lbo_b, tb, k0 + 8 * kc, n0, fb);
+            }
         }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0 && ok) {
+        // the copies of the last (up to kStages) stages land before the block
+        // ends, whether or not the MMA side consumed them
+        for (int j = issued > kStages ? issued - kStages : 0; j < issued; ++j)
+            if (!mbar_wait(saddr(&full[j % kStages]), (j / kStages) & 1)) ok = false;
+    } else if (tid == 32) {  // MMA issuer
+        int i = 0;
+        for (int kt = kt0; kt < kt1; ++kt, ++i) {
+            const int s = i % kStages;
+            if (!mbar_wait(saddr(&full[s]), (i / kStages) & 1)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t a_addr = saddr(smem + s * stage_bytes), b_addr = a_addr + a_bytes;
+            const uint32_t a = base + s * sbytes, b = a + a_bytes;
 #pragma unroll
             for (int ks = 0; ks < kBK / 16; ++ks)
-                umma_bf16(tmem, smem_desc(a_addr + ks * 256, 128, 1024), smem_desc(b_addr + ks * 256, 128, 1024),
-                          idesc, (kt > 0 || ks > 0) ? 1u : 0u);
-            umma_commit(saddr(&mbar[s]));
+                umma_bf16(tmem, smem_desc(a + ks * 2 * lbo_a, lbo_a, sbo), smem_desc(b + ks * 2 * lbo_b, lbo_b, sbo),
+                          idesc, (i > 0 || ks > 0) ? 1u : 0u);
+            umma_commit(saddr(&empty[s]));
         }
+        umma_commit(saddr(done));  // arrives once every MMA issued above has completed
     }
-    {
-        const int s = (nk - 1) & 1;  // completion of the last commit covers all earlier MMAs
-        ok = ok && mbar_wait(saddr(&mbar[s]), phase[s]);
-    }
+    ok = ok && mbar_wait(saddr(done), 0);
     ok = __syncthreads_and(ok ? 1 : 0) != 0;  // the tensor-memory loads below are warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (ok) {
+    if (ok && kt1 > kt0) {
         const int m = m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t v[16];
@@ -188,7 +215,7 @@ __device__ __forceinline__ void gemm_tn_umma(const __nv_bfloat16* __restrict__ A
                 }
             }
         }
-    } else if (tid == 0) {
+    } else if (!ok && tid == 0) {
         atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
