@@ -56,9 +56,13 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 #   bicgstab_packed_kernel: profiles/bicgstab_packed_kernel_stencil2d5_n144.md
 #   bicgstab_folded_kernel: profiles/bicgstab_folded_kernel_stencil2d5_n144.md
 #   refine_kernel:          profiles/refine_kernel_stencil2d9_n1024.md
+#   varsize_kernel:         profiles/varsize_kernel_uneven_n16-1024.md (first
+#                           20,000 systems of the uneven batch; per-system
+#                           bytes vary with n, so the scaling is approximate)
 TRAFFIC = {"bicgstab_packed_kernel": (135.8e6, 16384),
            "bicgstab_folded_kernel": (280.8e6, 32768),
-           "refine_kernel": (545.0e6, 4096)}
+           "refine_kernel": (545.0e6, 4096),
+           "varsize_kernel": (332.9e6, 20000)}
 
 
 def traffic_bytes(kernel, systems):
@@ -145,11 +149,11 @@ def subset_workload(wl, k):
 class Uniform:
     """bbs_solve over a shared-pattern batch (one launch per step)."""
 
-    def __init__(self, bbs, torch, dev, wl, fmt, opts_kw, label):
+    def __init__(self, bbs, torch, dev, wl, fmt, opts_kw, label, values_f32=False):
         self.bbs, self.torch, self.dev = bbs, torch, dev
         self.wl, self.fmt, self.label = wl, fmt, label
         self.A = wl.matrix(fmt)
-        self.dA = bbs.DeviceBatch.from_batch(self.A, dev)
+        self.dA = bbs.DeviceBatch.from_batch(self.A, dev, values_f32=values_f32)
         self.b = torch.as_tensor(wl.b, device=dev)
         self.x0 = torch.as_tensor(wl.x0, device=dev)
         self.x = self.x0.clone()
@@ -183,6 +187,14 @@ class Uniform:
     def compulsory_bytes(self):
         B, A = self.num_batch, self.A
         return 8 * (B * A.values.shape[1] + 3 * B * A.n) + 16 * B
+
+    def streamed_bytes(self):
+        """The matrix values re-read by every SpMV (two per iteration, plus the
+        initial and confirming residuals) as if nothing stayed on chip, plus
+        the compulsory vector bytes: the HBM traffic of an unstaged design."""
+        it = self.log.iters.cpu().numpy().astype(np.int64)
+        spmvs = 2 * it.sum() + 2 * self.num_batch
+        return 8 * self.A.values.shape[1] * int(spmvs) + 8 * 3 * self.num_batch * self.A.n + 16 * self.num_batch
 
     def summary(self):
         it = self.log.iters.cpu().numpy()
@@ -365,7 +377,8 @@ def pele_runs(bbs, torch, dev, num_batch=131072):
         res = {}
         for fmt in ("csr", "dense"):
             if fmt == "csr":
-                dA = bbs.DeviceBatch("csr", n, nnz, 0, torch.as_tensor(wl.pattern.row_ptrs, device=dev),
+                kmax = int(np.diff(wl.pattern.row_ptrs).max())  # the CSR row-length bound
+                dA = bbs.DeviceBatch("csr", n, nnz, kmax, torch.as_tensor(wl.pattern.row_ptrs, device=dev),
                                      torch.as_tensor(wl.pattern.col_idxs, device=dev), vals)
             else:
                 dense = torch.zeros(num_batch, n * n, dtype=torch.float64, device=dev)
@@ -373,10 +386,11 @@ def pele_runs(bbs, torch, dev, num_batch=131072):
                 pos = torch.as_tensor(rows * n + wl.pattern.col_idxs, device=dev)
                 dense[:, pos] = vals
                 dA = bbs.DeviceBatch("dense", n, nnz, 0, None, None, dense)
-            ms, it, conv = timed_solve(bbs, torch, h, dA, b, bbs.bbs_default_options())
+            opts = bbs.bbs_default_options()
+            ms, it, conv = timed_solve(bbs, torch, h, dA, b, opts)
             per_it = 4 * (nnz if fmt == "csr" else n * n) + 26 * n
             res[fmt] = {"ms": ms, "systems_per_s": num_batch / (ms / 1e3), "iters_mean": it,
-                        "converged": conv,
+                        "converged": conv, "launch": h.describe(dA, opts),
                         "fp64_tflops": num_batch * it * (4 * nnz + 26 * n) / (ms / 1e3) / 1e12,
                         "executed_tflops": num_batch * it * per_it / (ms / 1e3) / 1e12}
             del dA
@@ -485,6 +499,18 @@ def extras(bbs, torch, dev, stream, mhz):
                         "iterations": mix.summary(), "fp64_iterations": f64.summary(),
                         "roofline": roofline(mix, ms, mhz), "fp64_roofline": roofline(f64, ms64, mhz)}
         del f64, mix
+        torch.cuda.empty_cache()
+        # the same solve with the caller's FP32 copy of the values: the
+        # difference is the in-call FP32 conversion
+        wl = W.mixed_precision()
+        given = Uniform(bbs, torch, dev, wl, "ell",
+                        dict(precision="mixed", inner_tol=1e-2, max_iters=200, max_outer=30), wl.name,
+                        values_f32=True)
+        totg, _, _ = time_steps(given, torch, stream, 5, 2)
+        vg = given.num_batch * 5 / (totg / 1e3)
+        out["mixed"]["value_with_f32_copy_given"] = vg
+        out["mixed"]["conversion_ms_per_step"] = (tot - totg) / 5
+        del given
     except Exception as e:  # report, do not hide
         out["mixed"] = {"error": repr(e)}
     try:  # the same headline batch with one system per warp (no packing)
@@ -632,6 +658,11 @@ def main():
             "iterations": r.summary(),
             "compulsory_hbm": {"bytes": hbm_bytes, "GB/s": hbm_bytes / avg_solve_s / 1e9,
                                "frac_of_hbm": hbm_bytes / avg_solve_s / 1e9 / HBM_GBS}}
+    if hasattr(r, "streamed_bytes"):
+        sb = r.streamed_bytes()
+        line["streamed_matrix_hbm"] = {"bytes": sb, "GB/s": sb / avg_solve_s / 1e9,
+                                       "frac_of_hbm": sb / avg_solve_s / 1e9 / HBM_GBS,
+                                       "note": "values re-read by every SpMV, as an unstaged design would"}
     if rank == 0 and not args.no_e2e:
         line["e2e"] = r.e2e(max(2, min(args.steps, 5)))
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -639,8 +670,10 @@ def main():
 
         threads = oracle.num_threads()
         v, sample = r.cpu(threads, 10.0)
+        v1, sample1 = r.cpu(1, 3.0)
         line["cpu_baseline"] = {"value": v, "unit": "systems/s", "cores": threads, "kind": "oracle",
-                                "sample": sample + " (~10 s)"}
+                                "sample": sample + " (~10 s)",
+                                "one_thread": {"value": v1, "sample": sample1 + " (~3 s)"}}
     if rank == 0 and world == 1 and args.workload == "scale" and not args.no_extras and not args.systems:
         del r
         torch.cuda.empty_cache()

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/bbs.h: argument checks, the
 // launch-shape choice, the kernel dispatch over (solver, format, precision,
 // rows per thread) (Sec. 3.3's multi-level dispatch) and the host-buffer path.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -19,7 +20,11 @@ struct bbs_handle {
     int sms = 0;
     int max_smem_optin = 0;
     int max_threads = 1024;
-    cudaStream_t stream = nullptr;  // used by bbs_solve_host
+    // bbs_solve_host: two streams, so that one chunk's copies overlap the
+    // other's solve, and an event that orders the pattern copy before both
+    cudaStream_t stream = nullptr;
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t pattern_ready = nullptr;
     // device buffers owned for bbs_solve_host (grow only)
     void* buf[12] = {nullptr};
     size_t cap[12] = {0};
@@ -346,7 +351,11 @@ bbs_status bbs_create(bbs_handle** handle, int device) {
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&h->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&h->max_threads, cudaDevAttrMaxThreadsPerBlock, device);
-    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->pattern_ready, cudaEventDisableTiming)) != cudaSuccess) {
+        if (h->stream) cudaStreamDestroy(h->stream);
+        if (h->stream2) cudaStreamDestroy(h->stream2);
         delete h;
         return cuda_fail(e, "cudaStreamCreate");
     }
@@ -360,6 +369,8 @@ bbs_status bbs_destroy(bbs_handle* h) {
     for (int i = 0; i < 12; ++i)
         if (h->buf[i]) cudaFree(h->buf[i]);
     if (h->stream) cudaStreamDestroy(h->stream);
+    if (h->stream2) cudaStreamDestroy(h->stream2);
+    if (h->pattern_ready) cudaEventDestroy(h->pattern_ready);
     delete h;
     return BBS_OK;
 }
@@ -522,6 +533,11 @@ static bbs_status ensure(bbs_handle* h, int slot, size_t bytes, void** out) {
     return BBS_OK;
 }
 
+// Systems per chunk of bbs_solve_host: chunks alternate between the handle's
+// two streams, so the copies of one chunk overlap the solve of the other.
+// Per-system results do not depend on the chunking.
+constexpr size_t kHostChunk = 16384;
+
 bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const double* b_host,
                           double* x_host, const bbs_options* o, const bbs_log* log_host) {
     if (h == nullptr) return fail(BBS_ERR_INVALID_ARG, "null handle");
@@ -538,7 +554,7 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
     const size_t rp_bytes = Ah->fmt == BBS_FMT_CSR ? (n + 1) * 4 : 0;
     const size_t ci_bytes = Ah->fmt == BBS_FMT_CSR ? (size_t)Ah->nnz * 4
                             : Ah->fmt == BBS_FMT_ELL ? (size_t)Ah->ell_k * n * 4 : 0;
-    void *d_rp, *d_ci, *d_v, *d_v32, *d_b, *d_x, *d_it, *d_rr, *d_st, *d_in, *d_ws;
+    void *d_rp, *d_ci, *d_v, *d_v32, *d_b, *d_x, *d_it, *d_rr, *d_st, *d_in, *d_ws0, *d_ws1;
     if ((s = ensure(h, 0, rp_bytes, &d_rp)) || (s = ensure(h, 1, ci_bytes, &d_ci)) ||
         (s = ensure(h, 2, B * vps * 8, &d_v)) ||
         (s = ensure(h, 3, Ah->values_f32 ? B * vps * 4 : 0, &d_v32)) ||
@@ -547,38 +563,59 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
         (s = ensure(h, 8, B * 4, &d_st)) ||
         (s = ensure(h, 9, log_host->inner_iters ? B * 4 : 0, &d_in)))
         return s;
+    const size_t chunk = B <= kHostChunk ? B : kHostChunk;
+    const size_t nchunks = (B + chunk - 1) / chunk;
     bbs_batch_matrix Ad = *Ah;
     Ad.row_ptrs = static_cast<const int32_t*>(d_rp);
     Ad.col_idxs = static_cast<const int32_t*>(d_ci);
     Ad.values = static_cast<const double*>(d_v);
     Ad.values_f32 = static_cast<const float*>(d_v32);
-    size_t ws_bytes = 0;
+    Ad.num_batch = (int32_t)chunk;
+    size_t ws_bytes = 0;  // the largest chunk's workspace; one per stream
     if ((s = bbs_workspace_size(h, &Ad, o, &ws_bytes)) != BBS_OK) return s;
-    if ((s = ensure(h, 10, ws_bytes, &d_ws)) != BBS_OK) return s;
-    cudaStream_t st = h->stream;
-    cudaError_t e = cudaSuccess;
-#define BBS_CP(dst, src, bytes, kind)                                              \
-    if ((bytes) > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, kind, st)
-    BBS_CP(d_rp, Ah->row_ptrs, rp_bytes, cudaMemcpyHostToDevice);
-    BBS_CP(d_ci, Ah->col_idxs, ci_bytes, cudaMemcpyHostToDevice);
-    BBS_CP(d_v, Ah->values, B * vps * 8, cudaMemcpyHostToDevice);
-    if (Ah->values_f32) BBS_CP(d_v32, Ah->values_f32, B * vps * 4, cudaMemcpyHostToDevice);
-    BBS_CP(d_b, b_host, B * n * 8, cudaMemcpyHostToDevice);
-    BBS_CP(d_x, x_host, B * n * 8, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-    bbs_log dlog{static_cast<int32_t*>(d_it), static_cast<double*>(d_rr), static_cast<int32_t*>(d_st),
-                 static_cast<int32_t*>(d_in)};
-    if ((s = bbs_solve(h, &Ad, static_cast<const double*>(d_b), static_cast<double*>(d_x), o, &dlog,
-                       d_ws, ws_bytes, st)) != BBS_OK)
+    if ((s = ensure(h, 10, ws_bytes, &d_ws0)) != BBS_OK ||
+        (s = ensure(h, 11, nchunks > 1 ? ws_bytes : 0, &d_ws1)) != BBS_OK)
         return s;
-    BBS_CP(x_host, d_x, B * n * 8, cudaMemcpyDeviceToHost);
-    BBS_CP(log_host->iters, d_it, B * 4, cudaMemcpyDeviceToHost);
-    BBS_CP(log_host->rel_res, d_rr, B * 8, cudaMemcpyDeviceToHost);
-    BBS_CP(log_host->status, d_st, B * 4, cudaMemcpyDeviceToHost);
-    if (log_host->inner_iters) BBS_CP(log_host->inner_iters, d_in, B * 4, cudaMemcpyDeviceToHost);
+    cudaStream_t streams[2] = {h->stream, h->stream2};
+    cudaError_t e = cudaSuccess;
+#define BBS_CP(dst, src, bytes, kind, st)                                          \
+    if ((bytes) > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, kind, st)
+    BBS_CP(d_rp, Ah->row_ptrs, rp_bytes, cudaMemcpyHostToDevice, streams[0]);
+    BBS_CP(d_ci, Ah->col_idxs, ci_bytes, cudaMemcpyHostToDevice, streams[0]);
+    if (e == cudaSuccess) e = cudaEventRecord(h->pattern_ready, streams[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(streams[1], h->pattern_ready, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "pattern copy");
+    for (size_t c = 0; c < nchunks; ++c) {
+        cudaStream_t st = streams[c & 1];
+        const size_t c0 = c * chunk, cb = std::min(chunk, B - c0);
+        char* v = static_cast<char*>(d_v) + c0 * vps * 8;
+        char* v32 = Ah->values_f32 ? static_cast<char*>(d_v32) + c0 * vps * 4 : nullptr;
+        double* bd = static_cast<double*>(d_b) + c0 * n;
+        double* xd = static_cast<double*>(d_x) + c0 * n;
+        BBS_CP(v, reinterpret_cast<const char*>(Ah->values) + c0 * vps * 8, cb * vps * 8, cudaMemcpyHostToDevice, st);
+        if (Ah->values_f32)
+            BBS_CP(v32, reinterpret_cast<const char*>(Ah->values_f32) + c0 * vps * 4, cb * vps * 4,
+                   cudaMemcpyHostToDevice, st);
+        BBS_CP(bd, b_host + c0 * n, cb * n * 8, cudaMemcpyHostToDevice, st);
+        BBS_CP(xd, x_host + c0 * n, cb * n * 8, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+        bbs_batch_matrix Ac = Ad;
+        Ac.num_batch = (int32_t)cb;
+        Ac.values = reinterpret_cast<const double*>(v);
+        Ac.values_f32 = reinterpret_cast<const float*>(v32);
+        bbs_log dlog{static_cast<int32_t*>(d_it) + c0, static_cast<double*>(d_rr) + c0,
+                     static_cast<int32_t*>(d_st) + c0, d_in ? static_cast<int32_t*>(d_in) + c0 : nullptr};
+        if ((s = bbs_solve(h, &Ac, bd, xd, o, &dlog, (c & 1) ? d_ws1 : d_ws0, ws_bytes, st)) != BBS_OK) return s;
+        BBS_CP(x_host + c0 * n, xd, cb * n * 8, cudaMemcpyDeviceToHost, st);
+        BBS_CP(log_host->iters + c0, dlog.iters, cb * 4, cudaMemcpyDeviceToHost, st);
+        BBS_CP(log_host->rel_res + c0, dlog.rel_res, cb * 8, cudaMemcpyDeviceToHost, st);
+        BBS_CP(log_host->status + c0, dlog.status, cb * 4, cudaMemcpyDeviceToHost, st);
+        if (log_host->inner_iters) BBS_CP(log_host->inner_iters + c0, dlog.inner_iters, cb * 4, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    }
 #undef BBS_CP
-    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "solve");
+    for (cudaStream_t st : streams)
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "solve");
     return BBS_OK;
 }
 
