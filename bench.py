@@ -83,7 +83,7 @@ def parse():
     p.add_argument("--format", default="csr", choices=["csr", "ell", "dense"],
                    help="batch format of the scale workload")
     p.add_argument("--threads-per-system", type=int, default=0,
-                   help="launch shape of the scale workload (0: the library's choice)")
+                   help="launch shape of the scale and mixed workloads (0: the library's choice)")
     p.add_argument("--systems", type=int, default=0,
                    help="solve only the first N systems of the workload (profiling runs)")
     p.add_argument("--no-e2e", action="store_true")
@@ -330,8 +330,10 @@ def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0):
     if name == "mixed":
         wl = subset_workload(W.mixed_precision(), systems)
         # inner tolerance 1e-2: the fastest of 0.3 / 0.1 / 0.03 / 1e-2 / 1e-3 / 1e-4 in a sweep
-        return Uniform(bbs, torch, dev, wl, "ell",
-                       dict(precision="mixed", inner_tol=1e-2, max_iters=200, max_outer=30), wl.name)
+        kw = dict(precision="mixed", inner_tol=1e-2, max_iters=200, max_outer=30)
+        if tps:
+            kw["threads_per_system"] = tps
+        return Uniform(bbs, torch, dev, wl, "ell", kw, wl.name)
     if name == "mixed_fp64":
         wl = subset_workload(W.mixed_precision(), systems)
         return Uniform(bbs, torch, dev, wl, "ell", dict(max_iters=2000), wl.name)

@@ -533,10 +533,12 @@ static bbs_status ensure(bbs_handle* h, int slot, size_t bytes, void** out) {
     return BBS_OK;
 }
 
-// Systems per chunk of bbs_solve_host: chunks alternate between the handle's
-// two streams, so the copies of one chunk overlap the solve of the other.
-// Per-system results do not depend on the chunking.
-constexpr size_t kHostChunk = 16384;
+// bbs_solve_host cuts batches of more than kHostMinChunk systems into up to
+// kHostChunks chunks that alternate between the handle's two streams, so the
+// copies of one chunk overlap the solve of the other. Per-system results do
+// not depend on the chunking.
+constexpr size_t kHostMinChunk = 2048;
+constexpr size_t kHostChunks = 8;
 
 bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const double* b_host,
                           double* x_host, const bbs_options* o, const bbs_log* log_host) {
@@ -563,7 +565,7 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
         (s = ensure(h, 8, B * 4, &d_st)) ||
         (s = ensure(h, 9, log_host->inner_iters ? B * 4 : 0, &d_in)))
         return s;
-    const size_t chunk = B <= kHostChunk ? B : kHostChunk;
+    const size_t chunk = B <= kHostMinChunk ? B : std::max(kHostMinChunk, (B + kHostChunks - 1) / kHostChunks);
     const size_t nchunks = (B + chunk - 1) / chunk;
     bbs_batch_matrix Ad = *Ah;
     Ad.row_ptrs = static_cast<const int32_t*>(d_rp);
