@@ -533,10 +533,14 @@ static bbs_status ensure(bbs_handle* h, int slot, size_t bytes, void** out) {
     return BBS_OK;
 }
 
-// bbs_solve_host cuts batches of more than kHostMinChunk systems into up to
-// kHostChunks chunks that alternate between the handle's two streams, so the
-// copies of one chunk overlap the solve of the other. Per-system results do
-// not depend on the chunking.
+// bbs_solve_host cuts a batch into chunks of about kHostChunkBytes of input
+// (at most kHostChunks, at least kHostMinChunk systems each) that alternate
+// between the handle's two streams, so the copies of one chunk overlap the
+// solve of the other. Measured on GB300: 65,536 systems of 144 rows (503 MB)
+// run best in 4 chunks (8 chunks leave each solve a partial last wave);
+// 16,384 systems of 1,024 rows (1.5 GB) in 8. Per-system results do not
+// depend on the chunking.
+constexpr size_t kHostChunkBytes = 128u << 20;
 constexpr size_t kHostMinChunk = 2048;
 constexpr size_t kHostChunks = 8;
 
@@ -565,7 +569,9 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
         (s = ensure(h, 8, B * 4, &d_st)) ||
         (s = ensure(h, 9, log_host->inner_iters ? B * 4 : 0, &d_in)))
         return s;
-    const size_t chunk = B <= kHostMinChunk ? B : std::max(kHostMinChunk, (B + kHostChunks - 1) / kHostChunks);
+    const size_t in_bytes = B * (vps * (Ah->values_f32 ? 12 : 8) + 2 * n * 8);
+    const size_t want = std::min(kHostChunks, std::max<size_t>(1, (in_bytes + kHostChunkBytes - 1) / kHostChunkBytes));
+    const size_t chunk = std::min(B, std::max(kHostMinChunk, (B + want - 1) / want));
     const size_t nchunks = (B + chunk - 1) / chunk;
     bbs_batch_matrix Ad = *Ah;
     Ad.row_ptrs = static_cast<const int32_t*>(d_rp);
