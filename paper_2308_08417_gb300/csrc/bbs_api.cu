@@ -120,11 +120,10 @@ bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
     }
     const int t = o->threads_per_system;
     if (t == 4 || t == 8 || t == 16) {
-        if (o->solver == BBS_SOLVER_GMRES || o->precision != BBS_PRECISION_FP64 ||
-            o->precond == BBS_PREC_ILU0 || o->values_in_smem == -1)
+        if (o->solver == BBS_SOLVER_GMRES || o->precision != BBS_PRECISION_FP64 || o->values_in_smem == -1)
             return fail(BBS_ERR_UNSUPPORTED,
                         "threads_per_system %d (packed systems) is provided for FP64 BiCGSTAB and CG "
-                        "with Jacobi or no preconditioner and staged values", t);
+                        "with staged values", t);
     } else if (t != 0 && (t < 32 || t > 1024 || (t % 32) != 0)) {
         return fail(BBS_ERR_INVALID_ARG,
                     "threads_per_system must be 0, 4, 8, 16 or a multiple of 32 in [32, 1024]");
@@ -139,9 +138,9 @@ int max_row_len(const bbs_batch_matrix* A) { return A->fmt == BBS_FMT_ELL ? A->e
 // Shared memory of a packed system: xa [n_pad] | xb [n_pad] | values. The
 // slice is padded to 8 L bytes past a multiple of 128, so the groups that
 // share a half-warp's shared-memory wavefront start on different banks.
-size_t packed_slice(int n_pad, size_t vps, int L, size_t* stage_off) {
+size_t packed_slice(int n_pad, size_t vps, int L, size_t* stage_off, size_t extra = 0) {
     *stage_off = align_up(2 * (size_t)n_pad * 8, 16);
-    const size_t raw = *stage_off + align_up(vps * 8, 16);
+    const size_t raw = *stage_off + align_up(vps * 8, 16) + extra;
     const size_t shift = (size_t)(8 * L) % 128;
     return align_up(raw + 128 - shift, 128) - 128 + shift;
 }
@@ -169,8 +168,11 @@ constexpr int kPackedMinWarps = 8;
 bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_options* o, Plan* p) {
     const int n = A->n;
     const int tps = o->threads_per_system;
+    // ILU(0) packs too (BiCGSTAB on CSR; validate() rejects the rest): its
+    // factors are staged in the values' place and 1/u_ii after them
+    const bool ilu = o->precond == BBS_PREC_ILU0;
     const bool packable = o->solver != BBS_SOLVER_GMRES && o->precision == BBS_PRECISION_FP64 &&
-                          o->precond != BBS_PREC_ILU0 && o->values_in_smem != -1;
+                          o->values_in_smem != -1;
     // CSR packs through an ELL table of width ell_k (the caller's bound on
     // the row length); the library packs it only while the padding stays
     // small, and needs the bound in any case.
@@ -185,7 +187,7 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
         for (int L = tps ? tps : 4; L <= (tps ? tps : 16); L *= 2) {
             const int R = (n + L - 1) / L;
             size_t off = 0;
-            const size_t slice = packed_slice(n_pad, vps, L, &off);
+            const size_t slice = packed_slice(n_pad, vps, L, &off, ilu ? (size_t)n_pad * 8 : 0);
             const size_t smem = slice * (size_t)(32 / L);
             if (tps != 0) {
                 if (R > bbs::kMaxPackedR)
@@ -207,6 +209,10 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
             p->slice = slice;
             p->smem = smem;
             if (csr) p->ws_tables = align_up(2 * vps * 4, 256) + 256;
+            if (ilu) {
+                p->ilu = true;
+                p->ws_ilu = align_up(bbs::ilu_workspace_bytes(n), 256);
+            }
             return BBS_OK;
         }
     }
@@ -396,7 +402,8 @@ bbs_status bbs_describe(const bbs_handle* h, const bbs_batch_matrix* A, const bb
     std::memset(info, 0, sizeof *info);
     const bool mixed = o->precision == BBS_PRECISION_MIXED_IR;
     if (p.lanes < 32) {
-        info->kernel = o->solver == BBS_SOLVER_CG ? "cg_packed_kernel" : "bicgstab_packed_kernel";
+        info->kernel = p.ilu ? "bicgstab_ilu_packed_kernel"
+                       : o->solver == BBS_SOLVER_CG ? "cg_packed_kernel" : "bicgstab_packed_kernel";
         info->grid = (A->num_batch + 32 / p.lanes - 1) / (32 / p.lanes);
         info->threads_per_system = p.lanes;
     } else {
@@ -413,7 +420,7 @@ bbs_status bbs_describe(const bbs_handle* h, const bbs_batch_matrix* A, const bb
     info->rows_per_thread = p.R;
     info->smem_bytes = (int64_t)p.smem;
     info->values_staged = p.stage ? 1 : 0;
-    info->launches = A->num_batch == 0 ? 0 : 1 + ((p.ws_f32 > 0 || p.ilu || p.ws_tables > 0) ? 1 : 0);
+    info->launches = A->num_batch == 0 ? 0 : 1 + ((p.ws_f32 > 0 || p.ilu) ? 1 : 0) + (p.ws_tables > 0 ? 1 : 0);
     return BBS_OK;
 }
 
@@ -472,13 +479,16 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
             return cuda_fail(e, "FP32 conversion launch");
         P.values32 = f32;
     }
+    const int* csched = nullptr;
     if (p.ilu) {
         int* sched = reinterpret_cast<int*>(ws);
         if ((e = bbs::launch_ilu_analysis(A->n, A->row_ptrs, A->col_idxs, sched, st)) != cudaSuccess)
             return cuda_fail(e, "ILU(0) analysis launch");
+        csched = sched;
+    }
+    if (p.ilu && p.lanes == 32) {
         const void* fn = bbs::bicgstab_ilu_fn(p.R);
         if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-        const int* csched = sched;
         void* args[] = {&P, &csched};
         e = cudaLaunchKernel(fn, dim3((unsigned)A->num_batch), dim3((unsigned)p.threads), args, p.smem, st);
         return e == cudaSuccess ? BBS_OK : cuda_fail(e, "ILU(0) solver launch");
@@ -500,10 +510,11 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
             P.xflag = flag;
             P.xk = A->ell_k;
         }
-        const void* fn = o->solver == BBS_SOLVER_CG ? bbs::cg_packed_fn(A->fmt, p.lanes, p.R)
-                                                    : bbs::bicgstab_packed_fn(A->fmt, p.lanes, p.R);
+        const void* fn = p.ilu ? bbs::bicgstab_ilu_packed_fn(p.lanes, p.R)
+                         : o->solver == BBS_SOLVER_CG ? bbs::cg_packed_fn(A->fmt, p.lanes, p.R)
+                                                      : bbs::bicgstab_packed_fn(A->fmt, p.lanes, p.R);
         if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-        void* args[] = {&P};
+        void* args[] = {&P, &csched};  // the ILU(0) kernels take the schedule as a second argument
         const unsigned blocks = (unsigned)((A->num_batch + per_block - 1) / per_block);
         e = cudaLaunchKernel(fn, dim3(blocks), dim3(32), args, p.smem, st);
         return e == cudaSuccess ? BBS_OK : cuda_fail(e, "packed solver launch");

@@ -16,23 +16,12 @@
 
 #include <cuda_runtime.h>
 
+#include "bbs_ilu.cuh"
 #include "bbs_kernels.h"
 #include "bbs_solvers.cuh"
 
 namespace bbs {
 
-// Workspace layout (int32): nlevL, nlevU, levL_ptr[n+1], rowsL[n],
-// levU_ptr[n+1], rowsU[n], diag_pos[n], level scratch[n].
-struct IluSchedule {
-    const int* levL_ptr;
-    const int* rowsL;
-    const int* levU_ptr;
-    const int* rowsU;
-    const int* diag_pos;
-    int nlevL, nlevU;
-};
-
-__host__ __device__ inline size_t ilu_schedule_ints(int n) { return 2 + 2 * ((size_t)n + 1) + 4 * (size_t)n; }
 
 // Serial analysis of the shared pattern by one thread (n <= 2048).
 __global__ void ilu_analysis_kernel(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -159,14 +148,7 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) bicgstab_ilu_kernel(con
     double* udinv = lu + ((P.vps + 1) & ~(size_t)1);
     const Mat<double> A{P.values + (size_t)sys * P.vps, P.row_ptrs, P.cols, n, 0};
     const Op<FMT_CSR, R, double, double> op{A, nullptr};
-    IluSchedule S;
-    S.nlevL = sched[0];
-    S.nlevU = sched[1];
-    S.levL_ptr = sched + 2;
-    S.rowsL = S.levL_ptr + n + 1;
-    S.levU_ptr = S.rowsL + n;
-    S.rowsU = S.levU_ptr + n + 1;
-    S.diag_pos = S.rowsU + n;
+    const IluSchedule S = ilu_schedule(sched, n);
     stage_values(A.vals, lu, P.vps, tm);
     tm.sync();
     ilu_factor(A, lu, udinv, S, tm);
@@ -293,6 +275,11 @@ const void* bicgstab_ilu_fn(int R) {
         (const void*)bicgstab_ilu_kernel<5>, (const void*)bicgstab_ilu_kernel<6>,
         (const void*)bicgstab_ilu_kernel<7>, (const void*)bicgstab_ilu_kernel<8>};
     return kTable[R - 1];
+}
+
+const void* bicgstab_ilu_packed_fn(int L, int R) {
+    return L == 4 ? bicgstab_ilu_packed_fn_l4(R) : L == 8 ? bicgstab_ilu_packed_fn_l8(R)
+                                                        : bicgstab_ilu_packed_fn_l16(R);
 }
 
 size_t ilu_workspace_bytes(int n) { return ilu_schedule_ints(n) * sizeof(int); }

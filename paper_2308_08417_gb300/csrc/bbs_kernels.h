@@ -51,6 +51,11 @@ cudaError_t launch_csr_ell_tables(int n, int k, const int32_t* row_ptrs, const i
                                   int32_t* xsrc, int32_t* flag, cudaStream_t stream);
 
 const void* bicgstab_ilu_fn(int R);
+// Packed BiCGSTAB + ILU(0) on CSR (L = 4, 8, 16 lanes per system).
+const void* bicgstab_ilu_packed_fn(int L, int R);
+const void* bicgstab_ilu_packed_fn_l4(int R);
+const void* bicgstab_ilu_packed_fn_l8(int R);
+const void* bicgstab_ilu_packed_fn_l16(int R);
 size_t ilu_workspace_bytes(int n);
 cudaError_t launch_ilu_analysis(int n, const int32_t* row_ptrs, const int32_t* col_idxs, int* ws,
                                 cudaStream_t stream);
