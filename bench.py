@@ -435,7 +435,7 @@ def learned_run(bbs, torch, dev, eval_steps=192, num_batch=16384):
     from paper_2308_08417_gb300.learned import TimeStepped
 
     ts = W.time_stepped(num_batch=num_batch, steps=64 + eval_steps)
-    run = TimeStepped(ts, device=str(dev), hidden=256, seed=0, max_batch=4096)
+    run = TimeStepped(ts, device=str(dev), hidden=256, seed=0)
     rep = run.run(train_steps=64, eval_steps=eval_steps, epochs=6, batch=4096)
     s = rep.summary()
     s["workload"] = f"timestepped_stencil2d5_12x12_B{num_batch}_T{64 + eval_steps}"
@@ -525,6 +525,16 @@ def extras(bbs, torch, dev, stream, mhz):
         del ow
     except Exception as e:
         out["one_system_per_warp"] = {"error": repr(e)}
+    for solver in ("cg", "gmres"):  # the other Krylov solvers on the headline shape
+        try:
+            wl = W.plain_at_scale(symmetric=(solver == "cg"))
+            kr = Uniform(bbs, torch, dev, wl, "csr", dict(solver=solver), f"{solver}_{wl.name}")
+            tot, ms, _ = time_steps(kr, torch, stream, 5, 2)
+            out[solver] = {"workload": kr.label, "value": kr.num_batch * 5 / (tot / 1e3), "unit": "systems/s",
+                           "launch": kr.launch, "iterations": kr.summary()}
+            del kr
+        except Exception as e:
+            out[solver] = {"error": repr(e)}
     try:  # the same headline batch with the batched ILU(0) preconditioner
         il = Uniform(bbs, torch, dev, W.plain_at_scale(), "csr", dict(precond="ilu0"), "ilu0")
         tot, ms, _ = time_steps(il, torch, stream, 5, 2)

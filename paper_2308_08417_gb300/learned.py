@@ -74,7 +74,7 @@ class LearnedReport:
 
 
 class TimeStepped:
-    def __init__(self, ts: W.TimeSeries, device="cuda", hidden=256, seed=0, max_batch=4096):
+    def __init__(self, ts: W.TimeSeries, device="cuda", hidden=256, seed=0, max_batch=None):
         self.ts = ts
         self.dev = torch.device(device)
         self.h = B.Handle(self.dev.index or 0)
@@ -90,6 +90,10 @@ class TimeStepped:
         self.rhs = torch.empty_like(self.b0)
         self.opts = B.bbs_default_options()
         self.log = B.Log.empty(ts.num_batch, device=self.dev)
+        # rows the network handles per launch: the whole batch by default, so a
+        # prediction is one pass of four GEMMs over every system
+        if max_batch is None:
+            max_batch = max(4096, (ts.num_batch + 63) // 64 * 64)
         self.mlp = B.MLP(self.h, self.n, hidden=hidden, seed=seed, max_batch=max_batch)
         self.max_batch = max_batch
 
