@@ -456,14 +456,21 @@ def time_steps(r, torch, stream, steps, warmup, dist=None, sample_clocks=False, 
     clk = ClockSampler(dev_index) if sample_clocks else None
     if clk:
         clk.__enter__()
+    nvtx = torch.cuda.nvtx
+    nvtx.range_push("bbs.timed")  # NVTX ranges for timeline tools
     t0.record(stream)
     for k in range(steps):
+        nvtx.range_push("bbs.step")
         r.reset()
         ev[k][0].record(stream)
         r.step(stream)
         ev[k][1].record(stream)
+        nvtx.range_pop()
     t1.record(stream)
     torch.cuda.synchronize()
+    nvtx.range_pop()
+    if dist is not None:
+        dist.barrier()
     if clk:
         clk.__exit__()
     total_ms = t0.elapsed_time(t1)

@@ -178,6 +178,19 @@ typedef struct bbs_launch_info {
 bbs_status bbs_describe(const bbs_handle *handle, const bbs_batch_matrix *A, const bbs_options *opts,
                         bbs_launch_info *info);
 
+/* Check the shared pattern of A on the device, which the solvers trust:
+ *   CSR:   row_ptrs[0] = 0, row_ptrs non-decreasing, row_ptrs[n] = nnz;
+ *          columns in [0, n) and strictly increasing within each row; with
+ *          ell_k > 0, no row longer than ell_k;
+ *   ELL:   columns in [-1, n), strictly increasing within each row, and
+ *          padding (-1) only after the last stored entry of the row;
+ *   DENSE: nothing to check.
+ * *bad_rows receives the number of rows that break a rule (0: the pattern
+ * is valid). Reads only row_ptrs[0..n] and col_idxs[0..nnz) (CSR) or
+ * col_idxs[0..ell_k*n) (ELL), whatever they hold. Synchronous. Values are
+ * not inspected: non-finite values are reported per system (BBS_SYS_NAN). */
+bbs_status bbs_check_pattern(bbs_handle *handle, const bbs_batch_matrix *A, int32_t *bad_rows);
+
 /* Solve every system of the batch (Sec. 3.2-3.4: one thread block per system,
  * one launch for the batch; Sec. 2.1: x holds the initial guess on entry and
  * the solution on return). b, x: DEVICE [num_batch * n], system i at i*n.

@@ -104,6 +104,7 @@ def lib():
         L.bbs_workspace_size.argtypes = [C.c_void_p, P(bbs_batch_matrix), P(bbs_options),
                                          P(C.c_size_t)]
         L.bbs_describe.argtypes = [C.c_void_p, P(bbs_batch_matrix), P(bbs_options), P(bbs_launch_info)]
+        L.bbs_check_pattern.argtypes = [C.c_void_p, P(bbs_batch_matrix), P(C.c_int32)]
         L.bbs_solve.argtypes = [C.c_void_p, P(bbs_batch_matrix), C.c_void_p, C.c_void_p,
                                 P(bbs_options), P(bbs_log), C.c_void_p, C.c_size_t, C.c_void_p]
         L.bbs_solve_host.argtypes = [C.c_void_p, P(bbs_batch_matrix), C.c_void_p, C.c_void_p,
@@ -140,7 +141,7 @@ def lib():
         L.bbs_default_block_size.restype = C.c_int32
         L.bbs_last_error.restype = C.c_char_p
         L.bbs_version.restype = C.c_char_p
-        for name in ("bbs_default_options", "bbs_create", "bbs_destroy", "bbs_workspace_size", "bbs_describe",
+        for name in ("bbs_default_options", "bbs_create", "bbs_destroy", "bbs_workspace_size", "bbs_describe", "bbs_check_pattern",
                      "bbs_solve", "bbs_solve_host", "bbs_solve_noalloc", "bbs_var_default_tuning",
                      "bbs_var_plan_create", "bbs_var_solve", "bbs_var_plan_destroy", "bbs_var_tune",
                      "bbs_mlp_create", "bbs_mlp_destroy", "bbs_mlp_param_count", "bbs_mlp_get_params",
@@ -292,6 +293,13 @@ class Handle:
         return {"kernel": info.kernel.decode(), "grid": info.grid, "block": info.block,
                 "threads_per_system": info.threads_per_system, "rows": info.rows_per_thread,
                 "smem": info.smem_bytes, "staged": bool(info.values_staged), "launches": info.launches}
+
+    def check_pattern(self, A: DeviceBatch) -> int:
+        """bbs_check_pattern: the number of rows of A's shared pattern that break its format's rules."""
+        bad = C.c_int32()
+        s = A.struct()
+        _check(lib().bbs_check_pattern(self._h, C.byref(s), C.byref(bad)), "bbs_check_pattern")
+        return int(bad.value)
 
     def workspace(self, A: DeviceBatch, opts: bbs_options) -> torch.Tensor | None:
         nb = self.workspace_size(A, opts)

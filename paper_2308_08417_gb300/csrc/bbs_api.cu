@@ -424,6 +424,32 @@ bbs_status bbs_describe(const bbs_handle* h, const bbs_batch_matrix* A, const bb
     return BBS_OK;
 }
 
+bbs_status bbs_check_pattern(bbs_handle* h, const bbs_batch_matrix* A, int32_t* bad_rows) {
+    if (h == nullptr || A == nullptr || bad_rows == nullptr) return fail(BBS_ERR_INVALID_ARG, "null argument");
+    if (A->fmt < 0 || A->fmt > 2) return fail(BBS_ERR_INVALID_ARG, "unknown format %d", A->fmt);
+    if (A->n <= 0) return fail(BBS_ERR_INVALID_ARG, "n must be positive (got %d)", A->n);
+    *bad_rows = 0;
+    if (A->fmt == BBS_FMT_DENSE) return BBS_OK;
+    if (A->fmt == BBS_FMT_CSR && (A->nnz < 0 || A->row_ptrs == nullptr || A->col_idxs == nullptr || A->ell_k < 0))
+        return fail(BBS_ERR_INVALID_ARG, "CSR needs nnz >= 0, ell_k >= 0, row_ptrs and col_idxs");
+    if (A->fmt == BBS_FMT_ELL && (A->ell_k <= 0 || A->col_idxs == nullptr))
+        return fail(BBS_ERR_INVALID_ARG, "ELL needs ell_k > 0 and col_idxs");
+    cudaSetDevice(h->device);
+    int* d_bad = nullptr;
+    cudaError_t e = cudaMalloc(&d_bad, sizeof(int));
+    if (e != cudaSuccess) return fail(BBS_ERR_NO_MEMORY, "check buffer: %s", cudaGetErrorString(e));
+    int bad = 0;
+    if ((e = cudaMemsetAsync(d_bad, 0, sizeof(int), h->stream)) == cudaSuccess &&
+        (e = bbs::launch_check_pattern(A->fmt, A->n, A->nnz, A->ell_k, A->row_ptrs, A->col_idxs, d_bad, h->stream)) ==
+            cudaSuccess &&
+        (e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream)) == cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    cudaFree(d_bad);
+    if (e != cudaSuccess) return cuda_fail(e, "pattern check");
+    *bad_rows = bad;
+    return BBS_OK;
+}
+
 bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, double* x,
                      const bbs_options* o, const bbs_log* log, void* workspace,
                      size_t ws_bytes, void* stream) {

@@ -62,6 +62,51 @@ cudaError_t launch_csr_ell_tables(int n, int k, const int32_t* row_ptrs, const i
     return cudaGetLastError();
 }
 
+// One thread per row: counts the rows of a shared pattern that break the
+// format's rules (see bbs_check_pattern). Every read stays inside the arrays
+// whatever they hold.
+__global__ void check_pattern_kernel(int fmt, int n, int nnz, int k, const int32_t* __restrict__ rp,
+                                     const int32_t* __restrict__ cols, int* __restrict__ bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool ok = true;
+    if (fmt == FMT_CSR) {
+        const int e0 = rp[i], e1 = rp[i + 1];
+        if (i == 0 && e0 != 0) ok = false;
+        if (i == n - 1 && e1 != nnz) ok = false;
+        if (e0 < 0 || e1 < e0 || e1 > nnz) {
+            ok = false;
+        } else {
+            if (k > 0 && e1 - e0 > k) ok = false;
+            int prev = -1;
+            for (int e = e0; e < e1; ++e) {
+                const int c = cols[e];
+                if (c < 0 || c >= n || c <= prev) ok = false;
+                prev = c;
+            }
+        }
+    } else if (fmt == FMT_ELL) {
+        int prev = -1;
+        bool padded = false;
+        for (int j = 0; j < k; ++j) {
+            const int c = cols[(size_t)j * n + i];
+            if (c == -1) {
+                padded = true;
+                continue;
+            }
+            if (padded || c < 0 || c >= n || c <= prev) ok = false;
+            prev = c;
+        }
+    }
+    if (!ok) atomicAdd(bad, 1);
+}
+
+cudaError_t launch_check_pattern(int fmt, int n, int nnz, int k, const int32_t* rp, const int32_t* cols,
+                                 int* bad, cudaStream_t stream) {
+    check_pattern_kernel<<<(n + 127) / 128, 128, 0, stream>>>(fmt, n, nnz, k, rp, cols, bad);
+    return cudaGetLastError();
+}
+
 #define BBS_FRONT(S)                                   \
     const void* S##_fn(int fmt, int R) {               \
         if (fmt == FMT_CSR) return S##_fn_csr(R);      \

@@ -47,6 +47,8 @@ BBS_DECL_PACKED(bicgstab)
 BBS_DECL_PACKED(cg)
 #undef BBS_DECL_PACKED
 
+cudaError_t launch_check_pattern(int fmt, int n, int nnz, int k, const int32_t* rp, const int32_t* cols,
+                                 int* bad, cudaStream_t stream);
 cudaError_t launch_csr_ell_tables(int n, int k, const int32_t* row_ptrs, const int32_t* cols, int32_t* xcols,
                                   int32_t* xsrc, int32_t* flag, cudaStream_t stream);
 
