@@ -106,8 +106,9 @@ typedef struct {
     int32_t max_outer;     /* mixed: cap on refinement steps (>= 0) */
     int32_t threads_per_system; /* 0: library choice; 4, 8 or 16: packed
                                    systems, 32 / threads of them per warp in
-                                   lockstep (FP64 BiCGSTAB or CG with Jacobi
-                                   or no preconditioner, staged values,
+                                   lockstep (FP64 BiCGSTAB with Jacobi, none
+                                   or ILU(0), or CG; staged values; CSR needs
+                                   ell_k;
                                    ceil(n / threads) <= 10); else a multiple
                                    of 32 in [32, 1024] with
                                    ceil(n / threads) <= 8. The library choice
