@@ -249,3 +249,20 @@ def test_csr_row_longer_than_bound_reports_nan(bbs, handle):
         assert torch.equal(x, x0)
         g = gpu_solve(bbs, handle, A, wl.b, threads_per_system=tps)
         assert (g[3] == 0).all()
+
+
+def test_host_buffer_chunks_match_the_device_solve(bbs, handle):
+    """bbs_solve_host splits a batch of more than 128 MB of input into chunks
+    on two streams (here 20,001 systems, 154 MB, ragged last chunk); every
+    system's bits equal those of one device-buffer solve."""
+    wl = W.plain_at_scale(20001)
+    A = wl.matrix("csr")
+    dev = gpu_solve(bbs, handle, A, wl.b)
+    hA = bbs.DeviceBatch.from_batch(A, "cpu", pin=True)
+    hb = torch.as_tensor(wl.b).pin_memory()
+    hx = torch.zeros_like(hb).pin_memory()
+    log = bbs.Log.empty(20001, device="cpu", pin=True)
+    handle.solve_host(hA, hb, hx, bbs.bbs_default_options(), log)
+    assert np.array_equal(hx.numpy(), dev[0])
+    assert np.array_equal(log.iters.numpy(), dev[1]) and np.array_equal(log.status.numpy(), dev[3])
+    assert np.array_equal(log.rel_res.numpy(), dev[2])
