@@ -107,8 +107,8 @@ typedef struct {
     int32_t threads_per_system; /* 0: library choice; 4, 8 or 16: packed
                                    systems, 32 / threads of them per warp in
                                    lockstep (FP64 BiCGSTAB with Jacobi, none
-                                   or ILU(0), or CG; staged values; CSR needs
-                                   ell_k;
+                                   or ILU(0), CG or GMRES with Jacobi or none;
+                                   staged values; CSR needs ell_k;
                                    ceil(n / threads) <= 10); else a multiple
                                    of 32 in [32, 1024] with
                                    ceil(n / threads) <= 8. The library choice
@@ -149,7 +149,8 @@ bbs_status bbs_destroy(bbs_handle *handle);
 
 /* Bytes of DEVICE workspace bbs_solve needs for this problem (0 is possible).
  * Workspace use: the FP32 copy of the values in mixed mode when values_f32
- * is NULL, the GMRES Krylov basis when it does not fit in shared memory, the
+ * is NULL, the GMRES Krylov basis (always for packed systems, else when it
+ * does not fit in shared memory: (restart + 1) * n_pad doubles per system), the
  * ILU(0) level schedule of the shared pattern, and for packed systems on CSR
  * the pattern as an ELL column table (2 * ell_k * n int32 + 256 bytes). */
 bbs_status bbs_workspace_size(const bbs_handle *handle, const bbs_batch_matrix *A,
@@ -158,7 +159,8 @@ bbs_status bbs_workspace_size(const bbs_handle *handle, const bbs_batch_matrix *
 /* The launch bbs_solve makes for (A, opts) on this handle's device (the
  * multi-level dispatch of Sec. 3.3 made visible). Host-only: no GPU work,
  * A's arrays are not read. `kernel` points at a static string naming the
- * solver kernel: "bicgstab_packed_kernel", "cg_packed_kernel", "bicgstab_folded_kernel",
+ * solver kernel: "bicgstab_packed_kernel", "cg_packed_kernel", "gmres_packed_kernel",
+ * "bicgstab_ilu_packed_kernel", "bicgstab_folded_kernel",
  * "bicgstab_kernel", "bicgstab_ilu_kernel", "cg_kernel", "gmres_kernel" or
  * "refine_kernel". threads_per_system is the lanes of one system (4, 8 or
  * 16 when systems are packed 32 / lanes to a warp). launches counts every

@@ -120,10 +120,11 @@ bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
     }
     const int t = o->threads_per_system;
     if (t == 4 || t == 8 || t == 16) {
-        if (o->solver == BBS_SOLVER_GMRES || o->precision != BBS_PRECISION_FP64 || o->values_in_smem == -1)
+        if (o->precision != BBS_PRECISION_FP64 || o->values_in_smem == -1 ||
+            (o->solver == BBS_SOLVER_GMRES && o->precond == BBS_PREC_ILU0))
             return fail(BBS_ERR_UNSUPPORTED,
-                        "threads_per_system %d (packed systems) is provided for FP64 BiCGSTAB and CG "
-                        "with staged values", t);
+                        "threads_per_system %d (packed systems) is provided for FP64 solvers with staged "
+                        "values", t);
     } else if (t != 0 && (t < 32 || t > 1024 || (t % 32) != 0)) {
         return fail(BBS_ERR_INVALID_ARG,
                     "threads_per_system must be 0, 4, 8, 16 or a multiple of 32 in [32, 1024]");
@@ -171,8 +172,8 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
     // ILU(0) packs too (BiCGSTAB on CSR; validate() rejects the rest): its
     // factors are staged in the values' place and 1/u_ii after them
     const bool ilu = o->precond == BBS_PREC_ILU0;
-    const bool packable = o->solver != BBS_SOLVER_GMRES && o->precision == BBS_PRECISION_FP64 &&
-                          o->values_in_smem != -1;
+    const bool gmres = o->solver == BBS_SOLVER_GMRES;
+    const bool packable = o->precision == BBS_PRECISION_FP64 && o->values_in_smem != -1 && !(gmres && ilu);
     // CSR packs through an ELL table of width ell_k (the caller's bound on
     // the row length); the library packs it only while the padding stays
     // small, and needs the bound in any case.
@@ -187,7 +188,11 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
         for (int L = tps ? tps : 4; L <= (tps ? tps : 16); L *= 2) {
             const int R = (n + L - 1) / L;
             size_t off = 0;
-            const size_t slice = packed_slice(n_pad, vps, L, &off, ilu ? (size_t)n_pad * 8 : 0);
+            // after the values: 1/u_ii (ILU(0)) or the GMRES Hessenberg, rotations,
+            // right-hand side, solution and control words
+            const size_t mr = (size_t)o->gmres_restart;
+            const size_t extra = ilu ? (size_t)n_pad * 8 : gmres ? ((mr + 1) * mr + 2 * mr + (mr + 1) + mr + 2) * 8 : 0;
+            const size_t slice = packed_slice(n_pad, vps, L, &off, extra);
             const size_t smem = slice * (size_t)(32 / L);
             if (tps != 0) {
                 if (R > bbs::kMaxPackedR)
@@ -212,6 +217,10 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
             if (ilu) {
                 p->ilu = true;
                 p->ws_ilu = align_up(bbs::ilu_workspace_bytes(n), 256);
+            }
+            if (gmres) {  // the Krylov basis in the workspace, (m + 1) x n_pad per system
+                p->gmres_ws = true;
+                p->ws_gmres = (mr + 1) * (size_t)n_pad * 8 * (size_t)A->num_batch;
             }
             return BBS_OK;
         }
@@ -403,7 +412,8 @@ bbs_status bbs_describe(const bbs_handle* h, const bbs_batch_matrix* A, const bb
     const bool mixed = o->precision == BBS_PRECISION_MIXED_IR;
     if (p.lanes < 32) {
         info->kernel = p.ilu ? "bicgstab_ilu_packed_kernel"
-                       : o->solver == BBS_SOLVER_CG ? "cg_packed_kernel" : "bicgstab_packed_kernel";
+                       : o->solver == BBS_SOLVER_CG ? "cg_packed_kernel"
+                       : o->solver == BBS_SOLVER_GMRES ? "gmres_packed_kernel" : "bicgstab_packed_kernel";
         info->grid = (A->num_batch + 32 / p.lanes - 1) / (32 / p.lanes);
         info->threads_per_system = p.lanes;
     } else {
@@ -538,7 +548,8 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
         }
         const void* fn = p.ilu ? bbs::bicgstab_ilu_packed_fn(p.lanes, p.R)
                          : o->solver == BBS_SOLVER_CG ? bbs::cg_packed_fn(A->fmt, p.lanes, p.R)
-                                                      : bbs::bicgstab_packed_fn(A->fmt, p.lanes, p.R);
+                         : o->solver == BBS_SOLVER_GMRES ? bbs::gmres_packed_fn(A->fmt, p.lanes, p.R)
+                                                         : bbs::bicgstab_packed_fn(A->fmt, p.lanes, p.R);
         if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         void* args[] = {&P, &csched};  // the ILU(0) kernels take the schedule as a second argument
         const unsigned blocks = (unsigned)((A->num_batch + per_block - 1) / per_block);

@@ -1,4 +1,4 @@
-// Packed BiCGSTAB and CG kernels (32 / L systems per warp), DENSE format,
+// Packed BiCGSTAB, CG and GMRES kernels (32 / L systems per warp), DENSE format,
 // L = 16 lanes per system, R = 1..kMaxPackedR rows per lane.
 #include "bbs_kernels.h"
 #include "bbs_packed.cuh"
@@ -13,6 +13,7 @@ namespace bbs {
     return kTable[R - 1];
 static_assert(kMaxPackedR == 10, "tables cover R = 1..10");
 const void* bicgstab_packed_fn_dense_l16(int R) { BBS_TABLE(bicgstab_packed_kernel) }
+const void* gmres_packed_fn_dense_l16(int R) { BBS_TABLE(gmres_packed_kernel) }
 const void* cg_packed_fn_dense_l16(int R) { BBS_TABLE(cg_packed_kernel) }
 #undef BBS_TABLE
 }  // namespace bbs

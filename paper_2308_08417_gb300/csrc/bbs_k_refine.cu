@@ -132,6 +132,7 @@ BBS_FRONT(refine)
     }
 BBS_PACKED_FRONT(bicgstab)
 BBS_PACKED_FRONT(cg)
+BBS_PACKED_FRONT(gmres)
 #undef BBS_PACKED_FRONT
 
 }  // namespace bbs

@@ -29,8 +29,8 @@ BBS_DECL(gmres)
 BBS_DECL(refine)
 #undef BBS_DECL
 
-// Packed BiCGSTAB and CG (32 / L systems per warp): L = 4, 8 or 16 lanes
-// per system, R = 1..kMaxPackedR rows per lane.
+// Packed BiCGSTAB, CG and GMRES (32 / L systems per warp): L = 4, 8 or 16
+// lanes per system, R = 1..kMaxPackedR rows per lane.
 constexpr int kMaxPackedR = 10;
 #define BBS_DECL_PACKED(S)                       \
     const void* S##_packed_fn(int fmt, int L, int R); \
@@ -45,6 +45,7 @@ constexpr int kMaxPackedR = 10;
     const void* S##_packed_fn_dense_l16(int R);
 BBS_DECL_PACKED(bicgstab)
 BBS_DECL_PACKED(cg)
+BBS_DECL_PACKED(gmres)
 #undef BBS_DECL_PACKED
 
 cudaError_t launch_check_pattern(int fmt, int n, int nnz, int k, const int32_t* rp, const int32_t* cols,

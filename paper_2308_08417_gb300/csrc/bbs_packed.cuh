@@ -471,6 +471,265 @@ __device__ __forceinline__ void cg_packed_system(const PackedOp<FMT, R>& op, con
     write_result(io, x, status, iters, sqrt(res2 / nb2), 0, tm);
 }
 
+// ----------------------------------------------------------------- GMRES
+
+// Right-preconditioned GMRES(m) with Jacobi folded into the staged values
+// (As = A D^-1 on x~ = D x), packed like BiCGSTAB above; the method and its
+// rules are those of gmres_system: Arnoldi with modified Gram-Schmidt,
+// Givens rotations, the residual estimate |g_{j+1}| as the inner exit test,
+// the true residual after every cycle, restarts capped like the other
+// solvers' confirmations.
+// Each lane keeps its rows of the system's Krylov basis V [(m+1) x n_pad] in
+// the workspace (global memory, L2-resident: only the lane that writes a
+// row reads it), so shared memory holds only the staged values, the SpMV
+// input and the group's small arrays ext = H [(m+1) m] | cs [m] | sn [m] |
+// g [m+1] | y [m] | ctl [2 doubles]. The scalar Givens and back-substitution
+// work runs on the group's first lane, in lockstep with the other groups'.
+template <int FMT, int L, int R>
+__device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, const SysIO& io, bool valid,
+                                                    const SolveCfg& C, double* xa, double* ext, const Team& tm) {
+    const int n = io.n;
+    const int m = C.restart;
+    const bool jac = C.precond == 1;
+    const size_t vs = (size_t)((n + 1) & ~1);
+    double* V = C.ws;
+    double* H = ext;
+    double* cs = H + (m + 1) * m;
+    double* sn = cs + m;
+    double* g = sn + m;
+    double* y = g + m + 1;
+    int* ctl = reinterpret_cast<int*>(y + m);
+    const bool lead = tm.tid == 0;
+    if (jac) {
+        double dinv[R];
+        jacobi_setup<FMT, R>(op.A, true, dinv, tm);
+        op.scale(dinv, xa, tm);
+    }
+    double xs[R], w[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {  // x~ = D x0
+        const int row = tm.row(q);
+        const double d = (jac && row < n) ? diag_entry<FMT>(op.A, row) : 0.0;
+        const double x0 = row < n ? io.x[row] : 0.0;
+        xs[q] = (d != 0.0) ? d * x0 : x0;
+    }
+    double nb2;
+    {
+        double bb = 0.0;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int row = tm.row(q);
+            const double bq = row < n ? io.b[row] : 0.0;
+            bb = fma(bq, bq, bb);
+        }
+        double s0[1] = {bb};
+        group_sum<L>(s0, tm.lane);
+        nb2 = s0[0];
+    }
+    const int special = !finite(nb2) ? 1 : (nb2 == 0.0) ? 2 : 0;
+    bool active = valid && special == 0;
+    double beta2 = packed_residual<FMT, L, R>(op, io.b, xs, w, true, xa, tm, n);  // w = r
+    const double tau2 = (C.tol_type == 1) ? C.tol * C.tol * nb2 : C.tol * C.tol;
+    const double tau = sqrt(tau2);
+    int status = -1, it = 0, restarts = 0;
+    if (active) {
+        if (!finite(beta2)) {
+            status = ST_NAN;
+            active = false;
+        } else if (beta2 <= tau2) {
+            status = ST_CONVERGED;
+            active = false;
+        }
+    }
+    bool nan_exit = false;  // NAN inside a cycle: the log recomputes the residual
+    while (__any_sync(kFull, active)) {
+        if (active && it >= C.max_iters) {
+            status = ST_MAX_ITER;
+            active = false;
+        }
+        bool cyc = active;
+        const double binv = 1.0 / sqrt(beta2);
+        if (cyc) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int row = tm.row(q);
+                if (row < n) V[row] = w[q] * binv;
+            }
+            if (lead) {
+                for (int i = 0; i <= m; ++i) g[i] = 0.0;
+                g[0] = sqrt(beta2);
+            }
+        }
+        int k = 0;
+        bool singular = false, estimate_ok = false;
+        for (int j = 0; j < m; ++j) {
+            if (!__any_sync(kFull, cyc)) break;
+            if (cyc) ++it;
+            {
+                double u[R];
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int row = tm.row(q);
+                    u[q] = row < n ? V[(size_t)j * vs + row] : 0.0;
+                }
+                __syncwarp();  // every lane is done reading xa
+                put(xa, u, tm, n);
+            }
+            __syncwarp();
+            op.apply(xa, w, tm);
+            bool bad = false;
+            for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
+                double vr[R];
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int row = tm.row(q);
+                    vr[q] = row < n ? V[(size_t)i * vs + row] : 0.0;
+                }
+                double h[1] = {pdot(w, vr)};
+                group_sum<L>(h, tm.lane);
+                bad |= !finite(h[0]);
+#pragma unroll
+                for (int q = 0; q < R; ++q) w[q] = fma(-h[0], vr[q], w[q]);
+                if (cyc && lead) H[i * m + j] = h[0];
+            }
+            double hw[1] = {pdot(w, w)};
+            group_sum<L>(hw, tm.lane);
+            const double hn = sqrt(hw[0]);
+            bad |= !finite(hn);
+            if (cyc && bad) {
+                status = ST_NAN;
+                active = false;
+                cyc = false;
+                nan_exit = true;
+            }
+            if (cyc && lead) {
+                H[(j + 1) * m + j] = hn;
+                for (int i = 0; i < j; ++i) {
+                    const double a = H[i * m + j], c = H[(i + 1) * m + j];
+                    H[i * m + j] = cs[i] * a + sn[i] * c;
+                    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+                }
+                const double a = H[j * m + j];
+                const double denom = sqrt(a * a + hn * hn);
+                int c0, c1 = 0, c2 = 0;
+                if (denom == 0.0) {
+                    c0 = j;
+                    c1 = 1;
+                } else {
+                    cs[j] = a / denom;
+                    sn[j] = hn / denom;
+                    H[j * m + j] = denom;
+                    H[(j + 1) * m + j] = 0.0;
+                    g[j + 1] = -sn[j] * g[j];
+                    g[j] = cs[j] * g[j];
+                    c0 = j + 1;
+                    c2 = (hn == 0.0 || fabs(g[j + 1]) <= tau) ? 1 : 0;
+                }
+                ctl[0] = c0;
+                ctl[1] = c1 | (c2 << 1);
+            }
+            __syncwarp();
+            if (cyc) {  // the group's first lane wrote its ctl
+                k = ctl[0];
+                singular = ctl[1] & 1;
+                estimate_ok = (ctl[1] >> 1) & 1;
+            }
+            __syncwarp();  // ctl is rewritten in the next step
+            if (cyc && (singular || estimate_ok || it >= C.max_iters)) cyc = false;
+            if (cyc) {
+                const double hinv = 1.0 / hn;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int row = tm.row(q);
+                    if (row < n) V[(size_t)(j + 1) * vs + row] = w[q] * hinv;
+                }
+            }
+        }
+        // y = H(0:k,0:k)^-1 g(0:k) ; x~ += V y, for the groups still solving
+        const bool upd = active;
+        if (upd && lead) {
+            for (int i = k - 1; i >= 0; --i) {
+                double sum = g[i];
+                for (int l = i + 1; l < k; ++l) sum -= H[i * m + l] * y[l];
+                y[i] = sum / H[i * m + i];
+            }
+        }
+        __syncwarp();
+        if (upd) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int row = tm.row(q);
+                if (row < n) {
+                    double sum = 0.0;
+                    for (int i = 0; i < k; ++i) sum = fma(y[i], V[(size_t)i * vs + row], sum);
+                    xs[q] += sum;
+                }
+            }
+        }
+        if (__any_sync(kFull, upd)) {
+            __syncwarp();
+            const double res = packed_residual<FMT, L, R>(op, io.b, xs, w, upd, xa, tm, n);
+            if (upd) {
+                beta2 = res;
+                if (!finite(beta2)) {
+                    status = ST_NAN;
+                    active = false;
+                } else if (beta2 <= tau2) {
+                    status = ST_CONVERGED;
+                    active = false;
+                } else if (singular) {
+                    status = ST_BREAKDOWN;
+                    active = false;
+                } else if (it >= C.max_iters) {
+                    status = ST_MAX_ITER;
+                    active = false;
+                } else if (estimate_ok && ++restarts > kMaxRestarts) {
+                    status = ST_MAX_ITER;
+                    active = false;
+                }
+            }
+        }
+    }
+    double res2 = beta2;
+    if (__any_sync(kFull, valid && nan_exit)) {
+        __syncwarp();
+        double r[R];
+        const double res = packed_residual<FMT, L, R>(op, io.b, xs, r, false, xa, tm, n);
+        if (nan_exit) res2 = res;
+    }
+    if (!valid) return;
+    if (special == 1) {
+        if (tm.tid == 0) {
+            *io.iters = 0;
+            *io.rel_res = quiet_nan();
+            *io.status = ST_NAN;
+            if (io.inner != nullptr) *io.inner = 0;
+        }
+        return;
+    }
+    if (special == 2) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) xs[q] = 0.0;
+        write_result(io, xs, ST_CONVERGED, 0, 0.0, 0, tm);
+        return;
+    }
+    if (it > 0) {  // x = D^-1 x~
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int row = tm.row(q);
+            if (row >= n) continue;
+            const double d = jac ? diag_entry<FMT>(op.A, row) : 0.0;
+            io.x[row] = (d != 0.0) ? xs[q] / d : xs[q];
+        }
+    }
+    if (tm.tid == 0) {
+        *io.iters = it;
+        *io.rel_res = sqrt(res2 / nb2);
+        *io.status = status;
+        if (io.inner != nullptr) *io.inner = 0;
+    }
+}
+
 // ------------------------------------------------------------- kernels
 
 // Resident blocks an SM must hold, which sets the register cap (registers
@@ -551,6 +810,18 @@ __global__ void __launch_bounds__(32, packed_min_blocks(R)) bicgstab_packed_kern
     const PackedGroup<FMT, L, R> G(P, raw);
     if (packed_reject(P, G)) return;
     bicgstab_packed_system<FMT, L, R>(G.op, sys_io(P, G.sys), G.valid, solve_cfg(P, G.sys), G.sm, G.tm);
+}
+
+// GMRES: the group's small arrays follow its staged values in the slice.
+template <int FMT, int L, int R>
+__global__ void __launch_bounds__(32, packed_cg_min_blocks(R)) gmres_packed_kernel(const SolveParams P) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    const PackedGroup<FMT, L, R> G(P, raw);
+    if (packed_reject(P, G)) return;
+    const size_t count = FMT == FMT_CSR ? (size_t)P.xk * P.n : P.vps;
+    unsigned char* slice = raw + (size_t)((threadIdx.x & 31) / L) * P.slice;
+    double* ext = reinterpret_cast<double*>(slice + P.stage_off + ((count * 8 + 15) & ~(size_t)15));
+    gmres_packed_system<FMT, L, R>(G.op, sys_io(P, G.sys), G.valid, solve_cfg(P, G.sys), G.sm.xa, ext, G.tm);
 }
 
 template <int FMT, int L, int R>

@@ -1,4 +1,4 @@
-"""Packed BiCGSTAB and CG (several systems per warp in lockstep) against the CPU oracle.
+"""Packed BiCGSTAB, CG and GMRES (several systems per warp in lockstep) against the CPU oracle.
 
 Each aligned group of L = 4, 8 or 16 lanes owns one system. The tests cover:
 every lane width; rows per lane from 1 to the maximum of 10, ragged in n;
@@ -177,6 +177,53 @@ def test_cg_default_and_edges(bbs, handle):
     assert (g0[1] == 0).all() and (g0[3] == 1).all() and np.array_equal(g0[0], x0)
 
 
+@pytest.mark.parametrize("L", [4, 8, 16])
+@pytest.mark.parametrize("R,restart", [(1, 10), (3, 3), (6, 10), (9, 1), (10, 32)])
+def test_gmres_lane_widths_rows_and_restarts(bbs, handle, L, R, restart):
+    """Packed GMRES(m) on nonsymmetric batches: every lane width, rows per lane
+    up to 10, restart lengths from 1 to 32, a partly empty last warp."""
+    n = L * R - (L // 2 if R > 1 else 0)
+    pat, vals, b = stencil_batch(n, 37, 900 + 10 * L + R)
+    for fmt in ("csr", "ell"):
+        A = W.make_batch(pat, vals, fmt)
+        g = gpu_solve(bbs, handle, A, b, solver="gmres", gmres_restart=restart, threads_per_system=L,
+                      max_iters=2000)
+        r = oracle.solve_batch(A, b, solver="gmres", restart=restart, max_iters=2000)
+        D = W.to_dense(pat, vals).reshape(-1, n, n)
+        fails = compare(*g[:4], r[0], r[1], r[3], rel_host=host_rel_residual(D, g[0], b),
+                        label=f"gmres({restart}) {fmt} L={L} R={R} n={n}")
+        assert not fails, "\n".join(fails)
+
+
+def test_gmres_default_and_edges(bbs, handle):
+    wl = W.plain_at_scale(301)
+    A = wl.matrix("csr")
+    dA = bbs.DeviceBatch.from_batch(A, "cuda")
+    info = handle.describe(dA, bbs.bbs_default_options(solver="gmres"))
+    assert info["kernel"] == "gmres_packed_kernel" and info["threads_per_system"] == 16
+    vals = A.values.copy()
+    b = wl.b.copy()
+    b[3] = 0.0
+    vals[5, 7] = np.nan
+    b[9, 0] = np.inf
+    A2 = A.subset(np.arange(301))
+    A2.values = vals
+    x0 = np.full_like(b, 0.1)
+    for precond in ("jacobi", "none"):
+        g = gpu_solve(bbs, handle, A2, b, x0, solver="gmres", precond=precond)
+        r = oracle.solve_batch(A2, b, x0, solver="gmres", precond=precond)
+        assert g[3][5] == 3 and g[3][9] == 3 and g[3][3] == 0 and g[1][3] == 0 and (g[0][3] == 0).all()
+        keep = np.setdiff1d(np.arange(301), [5, 9])
+        fails = compare(g[0][keep], g[1][keep], g[2][keep], g[3][keep], r[0][keep], r[1][keep], r[3][keep],
+                        iter_tol=2 if precond == "jacobi" else 5, label=f"gmres edges {precond}")
+        assert not fails, "\n".join(fails)
+    g0 = gpu_solve(bbs, handle, A, wl.b, x0, solver="gmres", max_iters=0)
+    assert (g0[1] == 0).all() and (g0[3] == 1).all() and np.array_equal(g0[0], x0)
+    # a cap in the middle of a cycle stops every system with MAX_ITER after exactly 7 steps
+    g7 = gpu_solve(bbs, handle, A, wl.b, solver="gmres", max_iters=7)
+    assert (g7[3] == 1).all() and (g7[1] == 7).all()
+
+
 def test_results_do_not_depend_on_warp_partners(bbs, handle):
     """A system's bits do not depend on which systems share its warp."""
     wl = W.plain_at_scale(512)
@@ -211,7 +258,7 @@ def test_packed_argument_errors(bbs, handle):
     b = torch.as_tensor(wl.b, device="cuda")
     x = torch.zeros_like(b)
     log = bbs.Log.empty(4)
-    bad = [dict(threads_per_system=8, solver="gmres"), dict(threads_per_system=16, solver="gmres"),
+    bad = [dict(threads_per_system=8, solver="gmres", precond="ilu0"), dict(threads_per_system=16, solver="gmres", precision="mixed"),
            dict(threads_per_system=4, precision="mixed"), dict(threads_per_system=16, values_in_smem=-1),
            dict(threads_per_system=2), dict(threads_per_system=4, precond="ilu0")]
     for kw in bad:
