@@ -54,12 +54,17 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 # its own launch by systems (traffic is the compulsory bytes, which grow in
 # proportion). An entry is removed when its kernel changes.
 #   bicgstab_packed_kernel: profiles/bicgstab_packed_kernel_stencil2d5_n144.md
+#   cg_packed_kernel, gmres_packed_kernel, bicgstab_ilu_packed_kernel:
+#                           profiles/packed_cg_gmres_ilu_stencil2d5_n144.md
 #   bicgstab_folded_kernel: profiles/bicgstab_folded_kernel_stencil2d5_n144.md
 #   refine_kernel:          profiles/refine_kernel_stencil2d9_n1024.md
 #   varsize_kernel:         profiles/varsize_kernel_uneven_n16-1024.md (first
 #                           20,000 systems of the uneven batch; per-system
 #                           bytes vary with n, so the scaling is approximate)
 TRAFFIC = {"bicgstab_packed_kernel": (135.8e6, 16384),
+           "cg_packed_kernel": (133.7e6, 16384),
+           "gmres_packed_kernel": (338.5e6, 16384),
+           "bicgstab_ilu_packed_kernel": (135.2e6, 16384),
            "bicgstab_folded_kernel": (280.8e6, 32768),
            "refine_kernel": (545.0e6, 4096),
            "varsize_kernel": (332.9e6, 20000)}
@@ -82,6 +87,10 @@ def parse():
                    choices=["scale", "mixed", "uneven", "learned", "pele", "sweep"])
     p.add_argument("--format", default="csr", choices=["csr", "ell", "dense"],
                    help="batch format of the scale workload")
+    p.add_argument("--solver", default="bicgstab", choices=["bicgstab", "cg", "gmres"],
+                   help="solver of the scale workload (cg runs on its symmetrised copy)")
+    p.add_argument("--precond", default="jacobi", choices=["jacobi", "none", "ilu0"],
+                   help="preconditioner of the scale workload")
     p.add_argument("--threads-per-system", type=int, default=0,
                    help="launch shape of the scale and mixed workloads (0: the library's choice)")
     p.add_argument("--systems", type=int, default=0,
@@ -175,9 +184,20 @@ class Uniform:
         self.h.solve(self.dA, self.b, self.x, self.opts, self.log, self.ws, stream)
 
     def work(self):
-        """(algorithmic FLOPs of the last solve, arithmetic) per launch."""
-        A = self.A
-        per_it = 4 * A.nnz + 26 * A.n
+        """(algorithmic FLOPs of the last solve, arithmetic) per launch. Per
+        iteration: BiCGSTAB 4 nnz + 26 n; with ILU(0) two triangular solves
+        more, 2 (2 (nnz - n) + n); CG 2 nnz + 10 n; GMRES(m) per Arnoldi step j
+        2 nnz + (4 j + 7) n, taken at the cycle's mean j = (m - 1) / 2."""
+        A, o = self.A, self.opts
+        nnz = A.nnz if A.fmt == "csr" else int(np.count_nonzero(A.values[0]))
+        if o.solver == 1:
+            per_it = 2 * nnz + 10 * A.n
+        elif o.solver == 2:
+            per_it = 2 * nnz + (4 * (o.gmres_restart - 1) / 2 + 7) * A.n
+        else:
+            per_it = 4 * nnz + 26 * A.n
+            if o.precond == 2:
+                per_it += 2 * (2 * (nnz - A.n) + A.n)
         if self.mixed:
             inner = self.log.inner_iters.cpu().numpy().astype(np.int64)
             return float(inner.sum()) * per_it, "fp32"
@@ -326,7 +346,8 @@ class Uneven:
                 f"every 10th system of {self.vb.name}, repeated to {done} solves")
 
 
-def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0):
+def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0, solver="bicgstab",
+                precond="jacobi"):
     if name == "mixed":
         wl = subset_workload(W.mixed_precision(), systems)
         # inner tolerance 1e-2: the fastest of 0.3 / 0.1 / 0.03 / 1e-2 / 1e-3 / 1e-4 in a sweep
@@ -339,9 +360,12 @@ def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0):
         return Uniform(bbs, torch, dev, wl, "ell", dict(max_iters=2000), wl.name)
     if name == "uneven":
         return Uneven(bbs, torch, dev, W.uneven(systems or 100000), tune=tune)
-    wl = subset_workload(W.plain_at_scale(), systems)
+    wl = subset_workload(W.plain_at_scale(symmetric=(solver == "cg")), systems)
     opts = {"threads_per_system": tps} if tps else {}
+    opts.update(solver=solver, precond=precond)
     label = wl.name if fmt == "csr" else f"{wl.name}_{fmt}"
+    if (solver, precond) != ("bicgstab", "jacobi"):
+        label = f"{label}_{solver}+{precond}"
     return Uniform(bbs, torch, dev, wl, fmt, opts, label)
 
 
@@ -657,7 +681,7 @@ def main():
             print(json.dumps(line), flush=True)
         return
     r = make_runner(args.workload, bbs, torch, dev, args.systems, tune=not args.no_tune, fmt=args.format,
-                    tps=args.threads_per_system)
+                    tps=args.threads_per_system, solver=args.solver, precond=args.precond)
     total_ms, solve_ms, clocks = time_steps(r, torch, stream, args.steps, args.warmup, dist,
                                             sample_clocks=True, dev_index=local)
     total_ms = max_over_ranks(total_ms, dist, dev)  # the job's time is its slowest rank's
@@ -670,7 +694,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32" if r.mixed else "f64", "data": "synthetic",
             "config": {"workload": r.label, "num_batch_per_gpu": r.num_batch, "tol": 1e-10,
-                       "solver": "bicgstab+jacobi", "l2": "inputs larger than L2 (no flush)"},
+                       "solver": f"{args.solver}+{args.precond}" if args.workload == "scale" else "bicgstab+jacobi",
+                       "l2": "inputs larger than L2 (no flush)"},
             "gpu_launches": args.steps * r.launches_per_step,
             "launch": getattr(r, "launch", None),
             "clocks": clocks, "roofline": roofline(r, solve_ms, mhz),
