@@ -64,7 +64,6 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 TRAFFIC = {"bicgstab_packed_kernel": (135.8e6, 16384),
            "cg_packed_kernel": (133.7e6, 16384),
            "gmres_packed_kernel": (338.5e6, 16384),
-           "bicgstab_ilu_packed_kernel": (135.2e6, 16384),
            "bicgstab_folded_kernel": (280.8e6, 32768),
            "refine_kernel": (545.0e6, 4096),
            "varsize_kernel": (332.9e6, 20000)}

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/bbs.h"
+#include "bbs_ilu.cuh"
 #include "bbs_internal.h"
 #include "bbs_kernels.h"
 #include "bbs_params.h"
@@ -193,7 +194,8 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
             const size_t mr = (size_t)o->gmres_restart;
             const size_t extra = ilu ? (size_t)n_pad * 8 : gmres ? ((mr + 1) * mr + 2 * mr + (mr + 1) + mr + 2) * 8 : 0;
             const size_t slice = packed_slice(n_pad, vps, L, &off, extra);
-            const size_t smem = slice * (size_t)(32 / L);
+            // ILU(0) blocks also hold one copy of the pattern for their groups
+            const size_t smem = slice * (size_t)(32 / L) + (ilu ? bbs::ilu_pattern_smem(n, A->ell_k) : 0);
             if (tps != 0) {
                 if (R > bbs::kMaxPackedR)
                     return fail(BBS_ERR_INVALID_ARG, "threads_per_system %d leaves %d rows per lane (max %d)",

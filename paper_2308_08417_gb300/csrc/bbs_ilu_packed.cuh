@@ -24,21 +24,61 @@
 
 namespace bbs {
 
-// The pattern as the packed ILU kernels read it: ELL column table (k slots,
-// -1 past the row end), the row pointers (row lengths) and the schedule.
+// The pattern as the packed ILU kernels read it. The dependent steps of the
+// factorisation and the triangular solves read it from a block-shared copy
+// in shared memory (16-bit indices: n <= 160): the ELL column table (k
+// slots, -1 past the row end), each row's length and diagonal slot, and the
+// level schedule. The SpMV gathers through the global tables (xcols, xsrc).
 struct IluPattern {
-    const int32_t* xcols;
-    const int32_t* xsrc;
-    const int32_t* rp;
+    const int32_t* xcols;  // global
+    const int32_t* xsrc;   // global
     int n, k;
-    IluSchedule S;
-    __device__ __forceinline__ int len(int i) const { return min(k, ldg(rp + i + 1) - ldg(rp + i)); }
-    __device__ __forceinline__ int col(int e, int i) const { return ldg(xcols + (size_t)e * n + i); }
-    __device__ __forceinline__ int dslot(int i) const {  // slot of a_ii, -1 if absent
-        const int d = S.diag_pos[i];
-        return d >= 0 ? d - ldg(rp + i) : -1;
-    }
+    int nlevL, nlevU;
+    const int16_t* scols;  // shared [k n]
+    const int16_t* slen;   // shared [n]
+    const int16_t* sdslot; // shared [n], -1 without a stored diagonal
+    const int16_t* slevL;  // shared [nlevL + 1]
+    const int16_t* srowsL; // shared [n]
+    const int16_t* slevU;  // shared [nlevU + 1]
+    const int16_t* srowsU; // shared [n]
+    __device__ __forceinline__ int len(int i) const { return slen[i]; }
+    __device__ __forceinline__ int col(int e, int i) const { return scols[e * n + i]; }
+    __device__ __forceinline__ int dslot(int i) const { return sdslot[i]; }
 };
+
+// The whole warp copies the pattern into `dst` (ilu_pattern_smem bytes).
+__device__ __forceinline__ void ilu_pattern_stage(IluPattern& Pt, const IluSchedule& S, const int32_t* rp,
+                                                  int16_t* dst, int lane) {
+    const int n = Pt.n, k = Pt.k;
+    int16_t* cols = dst;
+    int16_t* len = cols + (size_t)k * n;
+    int16_t* dsl = len + n;
+    int16_t* levL = dsl + n;
+    int16_t* rowsL = levL + n + 1;
+    int16_t* levU = rowsL + n;
+    int16_t* rowsU = levU + n + 1;
+    for (int i = lane; i < k * n; i += 32) cols[i] = (int16_t)ldg(Pt.xcols + i);
+    for (int i = lane; i < n; i += 32) {
+        const int r0 = ldg(rp + i);
+        len[i] = (int16_t)min(k, ldg(rp + i + 1) - r0);
+        const int d = S.diag_pos[i];
+        dsl[i] = (int16_t)(d >= 0 ? d - r0 : -1);
+        rowsL[i] = (int16_t)S.rowsL[i];
+        rowsU[i] = (int16_t)S.rowsU[i];
+    }
+    for (int l = lane; l <= S.nlevL; l += 32) levL[l] = (int16_t)S.levL_ptr[l];
+    for (int l = lane; l <= S.nlevU; l += 32) levU[l] = (int16_t)S.levU_ptr[l];
+    __syncwarp();
+    Pt.scols = cols;
+    Pt.slen = len;
+    Pt.sdslot = dsl;
+    Pt.slevL = levL;
+    Pt.srowsL = rowsL;
+    Pt.slevU = levU;
+    Pt.srowsU = rowsU;
+    Pt.nlevL = S.nlevL;
+    Pt.nlevU = S.nlevU;
+}
 
 // y = A x with A's values read from global memory in ELL order.
 template <int R>
@@ -68,16 +108,15 @@ __device__ __forceinline__ double pivot_inverse(const IluPattern& Pt, const doub
 // In-place ILU(0) of the group's staged values, level by level.
 __device__ __forceinline__ void ilu_factor_packed(const IluPattern& Pt, double* lu, double* udinv,
                                                   const Team& tm) {
-    const IluSchedule& S = Pt.S;
     const int n = Pt.n;
-    for (int t = S.levL_ptr[0] + tm.tid; t < S.levL_ptr[1]; t += tm.nt) {  // rows without a lower part
-        const int i = S.rowsL[t];
+    for (int t = Pt.slevL[0] + tm.tid; t < Pt.slevL[1]; t += tm.nt) {  // rows without a lower part
+        const int i = Pt.srowsL[t];
         udinv[i] = pivot_inverse(Pt, lu, i);
     }
     __syncwarp();
-    for (int l = 1; l < S.nlevL; ++l) {
-        for (int t = S.levL_ptr[l] + tm.tid; t < S.levL_ptr[l + 1]; t += tm.nt) {
-            const int i = S.rowsL[t];
+    for (int l = 1; l < Pt.nlevL; ++l) {
+        for (int t = Pt.slevL[l] + tm.tid; t < Pt.slevL[l + 1]; t += tm.nt) {
+            const int i = Pt.srowsL[t];
             const int len = Pt.len(i);
             for (int e = 0; e < len; ++e) {
                 const int kk = Pt.col(e, i);
@@ -102,11 +141,10 @@ __device__ __forceinline__ void ilu_factor_packed(const IluPattern& Pt, double* 
 // buf = U^-1 L^-1 buf, in place, by the group.
 __device__ __forceinline__ void ilu_apply_packed(const IluPattern& Pt, const double* lu, const double* udinv,
                                                  double* buf, const Team& tm) {
-    const IluSchedule& S = Pt.S;
     const int n = Pt.n;
-    for (int l = 1; l < S.nlevL; ++l) {
-        for (int t = S.levL_ptr[l] + tm.tid; t < S.levL_ptr[l + 1]; t += tm.nt) {
-            const int i = S.rowsL[t];
+    for (int l = 1; l < Pt.nlevL; ++l) {
+        for (int t = Pt.slevL[l] + tm.tid; t < Pt.slevL[l + 1]; t += tm.nt) {
+            const int i = Pt.srowsL[t];
             double sum = buf[i];
             const int len = Pt.len(i);
             for (int e = 0; e < len; ++e) {
@@ -118,9 +156,9 @@ __device__ __forceinline__ void ilu_apply_packed(const IluPattern& Pt, const dou
         }
         __syncwarp();
     }
-    for (int l = 0; l < S.nlevU; ++l) {
-        for (int t = S.levU_ptr[l] + tm.tid; t < S.levU_ptr[l + 1]; t += tm.nt) {
-            const int i = S.rowsU[t];
+    for (int l = 0; l < Pt.nlevU; ++l) {
+        for (int t = Pt.slevU[l] + tm.tid; t < Pt.slevU[l + 1]; t += tm.nt) {
+            const int i = Pt.srowsU[t];
             double sum = buf[i];
             for (int e = Pt.len(i) - 1; e >= 0; --e) {
                 const int j = Pt.col(e, i);
@@ -352,7 +390,8 @@ __device__ __forceinline__ void bicgstab_ilu_packed_system(const IluPattern& Pt,
 }
 
 // One warp per block, 32 / L systems per warp; shared memory per group of
-// P.slice bytes: xa [n_pad] | xb [n_pad] | lu at P.stage_off | udinv after lu.
+// P.slice bytes: xa [n_pad] | xb [n_pad] | lu at P.stage_off | udinv after
+// lu; after the 32 / L slices, the block's copy of the pattern.
 template <int L, int R>
 __global__ void __launch_bounds__(32, packed_cg_min_blocks(R))
     bicgstab_ilu_packed_kernel(const SolveParams P, const int* sched) {
@@ -381,10 +420,10 @@ __global__ void __launch_bounds__(32, packed_cg_min_blocks(R))
     IluPattern Pt;
     Pt.xcols = P.xcols;
     Pt.xsrc = P.xsrc;
-    Pt.rp = P.row_ptrs;
     Pt.n = P.n;
     Pt.k = P.xk;
-    Pt.S = ilu_schedule(sched, P.n);
+    ilu_pattern_stage(Pt, ilu_schedule(sched, P.n), P.row_ptrs,
+                      reinterpret_cast<int16_t*>(raw + (size_t)S * P.slice), lane);
     const double* vals = P.values + (size_t)sys * P.vps;
     for (size_t i = tm.tid; i < cells; i += L) {
         const int src = ldg(P.xsrc + i);
