@@ -174,7 +174,9 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
     // factors are staged in the values' place and 1/u_ii after them
     const bool ilu = o->precond == BBS_PREC_ILU0;
     const bool gmres = o->solver == BBS_SOLVER_GMRES;
-    const bool packable = o->precision == BBS_PRECISION_FP64 && o->values_in_smem != -1 && !(gmres && ilu);
+    // (the packed ILU(0) kernel keeps CSR indices in 16 bits)
+    const bool packable = o->precision == BBS_PRECISION_FP64 && o->values_in_smem != -1 && !(gmres && ilu) &&
+                          !(ilu && A->nnz >= 32768);
     // CSR packs through an ELL table of width ell_k (the caller's bound on
     // the row length); the library packs it only while the padding stays
     // small, and needs the bound in any case.

@@ -28,13 +28,16 @@ namespace bbs {
 // factorisation and the triangular solves read it from a block-shared copy
 // in shared memory (16-bit indices: n <= 160): the ELL column table (k
 // slots, -1 past the row end), each row's length and diagonal slot, and the
-// level schedule. The SpMV gathers through the global tables (xcols, xsrc).
+// level schedule; the SpMV also reads the map from slots to CSR values there
+// (CSR indices below 2^15: nnz <= n^2 <= 25,600) and gathers the values
+// themselves from global memory.
 struct IluPattern {
     const int32_t* xcols;  // global
     const int32_t* xsrc;   // global
     int n, k;
     int nlevL, nlevU;
     const int16_t* scols;  // shared [k n]
+    const int16_t* ssrc;   // shared [k n], -1 past the row end
     const int16_t* slen;   // shared [n]
     const int16_t* sdslot; // shared [n], -1 without a stored diagonal
     const int16_t* slevL;  // shared [nlevL + 1]
@@ -51,13 +54,17 @@ __device__ __forceinline__ void ilu_pattern_stage(IluPattern& Pt, const IluSched
                                                   int16_t* dst, int lane) {
     const int n = Pt.n, k = Pt.k;
     int16_t* cols = dst;
-    int16_t* len = cols + (size_t)k * n;
+    int16_t* src = cols + (size_t)k * n;
+    int16_t* len = src + (size_t)k * n;
     int16_t* dsl = len + n;
     int16_t* levL = dsl + n;
     int16_t* rowsL = levL + n + 1;
     int16_t* levU = rowsL + n;
     int16_t* rowsU = levU + n + 1;
-    for (int i = lane; i < k * n; i += 32) cols[i] = (int16_t)ldg(Pt.xcols + i);
+    for (int i = lane; i < k * n; i += 32) {
+        cols[i] = (int16_t)ldg(Pt.xcols + i);
+        src[i] = (int16_t)ldg(Pt.xsrc + i);
+    }
     for (int i = lane; i < n; i += 32) {
         const int r0 = ldg(rp + i);
         len[i] = (int16_t)min(k, ldg(rp + i + 1) - r0);
@@ -70,6 +77,7 @@ __device__ __forceinline__ void ilu_pattern_stage(IluPattern& Pt, const IluSched
     for (int l = lane; l <= S.nlevU; l += 32) levU[l] = (int16_t)S.levU_ptr[l];
     __syncwarp();
     Pt.scols = cols;
+    Pt.ssrc = src;
     Pt.slen = len;
     Pt.sdslot = dsl;
     Pt.slevL = levL;
@@ -90,9 +98,9 @@ __device__ __forceinline__ void spmv_gather(const IluPattern& Pt, const double* 
         double sum = 0.0;
         if (row < Pt.n) {
             for (int j = 0; j < Pt.k; ++j) {
-                const size_t i = (size_t)j * Pt.n + row;
-                const int col = ldg(Pt.xcols + i);
-                if (col >= 0) sum = fma(ldg(vals + ldg(Pt.xsrc + i)), xs[col], sum);
+                const int i = j * Pt.n + row;
+                const int col = Pt.scols[i];
+                if (col >= 0) sum = fma(ldg(vals + Pt.ssrc[i]), xs[col], sum);
             }
         }
         y[q] = sum;
