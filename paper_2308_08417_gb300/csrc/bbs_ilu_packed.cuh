@@ -6,14 +6,15 @@
 // schedule: every group factors and solves the same rows of the same level
 // at the same time, and a level of up to L rows takes one pass of the group.
 // Per group, shared memory holds
-//   xa [n_pad] | xb [n_pad] | lu [k n] (ELL order) | udinv [n_pad]
+//   xa [n_pad] | xb [n_pad] | lu [k n] (ELL order)
 // where lu starts as the system's values gathered into ELL order through the
 // per-solve CSR column table (slot j of row i at j n + i) and is factored in
 // place: for each stored k < i of row i, l_ik = a_ik / u_kk and
 // a_ij -= l_ik u_kj for every j > k stored in rows i and k (IKJ form, rows
 // level by level). A zero pivot counts as 1, as in the one-system kernel.
-// udinv[k] = 1 / u_kk is formed as soon as row k is final, so each lower
-// entry costs one multiply. M^-1 = U^-1 L^-1 is applied in place in xa / xb.
+// As soon as row k is final its diagonal slot is overwritten with 1 / u_kk
+// (later rows read u_k only right of the diagonal), so each lower entry costs
+// one multiply and the backward solve needs no separate inverse. M^-1 = U^-1 L^-1 is applied in place in xa / xb.
 // The SpMV reads the original values from global memory through the same
 // table (they stay in L1/L2). The method, its stopping rules and its log
 // are those of bicgstab_ilu_kernel.
@@ -26,10 +27,10 @@ namespace bbs {
 
 // The pattern as the packed ILU kernels read it. The dependent steps of the
 // factorisation and the triangular solves read it from a block-shared copy
-// in shared memory (16-bit indices: n <= 160): the ELL column table (k
-// slots, -1 past the row end), each row's length and diagonal slot, and the
-// level schedule; the SpMV also reads the map from slots to CSR values there
-// (CSR indices below 2^15: nnz <= n^2 <= 25,600) and gathers the values
+// in shared memory (n <= 160): the ELL column table (16-bit, -1 past the row
+// end), each row's length and diagonal slot and the level schedule (8-bit);
+// the SpMV also reads the map from slots to CSR values there (16-bit: CSR
+// indices stay below 2^15 as nnz <= n^2 <= 25,600) and gathers the values
 // themselves from global memory.
 struct IluPattern {
     const int32_t* xcols;  // global
@@ -38,15 +39,15 @@ struct IluPattern {
     int nlevL, nlevU;
     const int16_t* scols;  // shared [k n]
     const int16_t* ssrc;   // shared [k n], -1 past the row end
-    const int16_t* slen;   // shared [n]
-    const int16_t* sdslot; // shared [n], -1 without a stored diagonal
-    const int16_t* slevL;  // shared [nlevL + 1]
-    const int16_t* srowsL; // shared [n]
-    const int16_t* slevU;  // shared [nlevU + 1]
-    const int16_t* srowsU; // shared [n]
+    const uint8_t* slen;   // shared [n]
+    const uint8_t* sdslot; // shared [n], 255 without a stored diagonal
+    const uint8_t* slevL;  // shared [nlevL + 1]
+    const uint8_t* srowsL; // shared [n]
+    const uint8_t* slevU;  // shared [nlevU + 1]
+    const uint8_t* srowsU; // shared [n]
     __device__ __forceinline__ int len(int i) const { return slen[i]; }
     __device__ __forceinline__ int col(int e, int i) const { return scols[e * n + i]; }
-    __device__ __forceinline__ int dslot(int i) const { return sdslot[i]; }
+    __device__ __forceinline__ int dslot(int i) const { return sdslot[i] == 255 ? -1 : sdslot[i]; }
 };
 
 // The whole warp copies the pattern into `dst` (ilu_pattern_smem bytes).
@@ -55,26 +56,26 @@ __device__ __forceinline__ void ilu_pattern_stage(IluPattern& Pt, const IluSched
     const int n = Pt.n, k = Pt.k;
     int16_t* cols = dst;
     int16_t* src = cols + (size_t)k * n;
-    int16_t* len = src + (size_t)k * n;
-    int16_t* dsl = len + n;
-    int16_t* levL = dsl + n;
-    int16_t* rowsL = levL + n + 1;
-    int16_t* levU = rowsL + n;
-    int16_t* rowsU = levU + n + 1;
+    uint8_t* len = reinterpret_cast<uint8_t*>(src + (size_t)k * n);
+    uint8_t* dsl = len + n;
+    uint8_t* levL = dsl + n;
+    uint8_t* rowsL = levL + n + 1;
+    uint8_t* levU = rowsL + n;
+    uint8_t* rowsU = levU + n + 1;
     for (int i = lane; i < k * n; i += 32) {
         cols[i] = (int16_t)ldg(Pt.xcols + i);
         src[i] = (int16_t)ldg(Pt.xsrc + i);
     }
     for (int i = lane; i < n; i += 32) {
         const int r0 = ldg(rp + i);
-        len[i] = (int16_t)min(k, ldg(rp + i + 1) - r0);
+        len[i] = (uint8_t)min(k, ldg(rp + i + 1) - r0);
         const int d = S.diag_pos[i];
-        dsl[i] = (int16_t)(d >= 0 ? d - r0 : -1);
-        rowsL[i] = (int16_t)S.rowsL[i];
-        rowsU[i] = (int16_t)S.rowsU[i];
+        dsl[i] = (uint8_t)(d >= 0 ? d - r0 : 255);
+        rowsL[i] = (uint8_t)S.rowsL[i];
+        rowsU[i] = (uint8_t)S.rowsU[i];
     }
-    for (int l = lane; l <= S.nlevL; l += 32) levL[l] = (int16_t)S.levL_ptr[l];
-    for (int l = lane; l <= S.nlevU; l += 32) levU[l] = (int16_t)S.levU_ptr[l];
+    for (int l = lane; l <= S.nlevL; l += 32) levL[l] = (uint8_t)S.levL_ptr[l];
+    for (int l = lane; l <= S.nlevU; l += 32) levU[l] = (uint8_t)S.levU_ptr[l];
     __syncwarp();
     Pt.scols = cols;
     Pt.ssrc = src;
@@ -107,19 +108,27 @@ __device__ __forceinline__ void spmv_gather(const IluPattern& Pt, const double* 
     }
 }
 
-__device__ __forceinline__ double pivot_inverse(const IluPattern& Pt, const double* lu, int i) {
+// Overwrite row i's finished diagonal u_ii with 1 / u_ii (1 for a zero or
+// missing pivot).
+__device__ __forceinline__ void invert_pivot(const IluPattern& Pt, double* lu, int i) {
     const int d = Pt.dslot(i);
-    const double u = d >= 0 ? lu[(size_t)d * Pt.n + i] : 0.0;
-    return (u != 0.0) ? 1.0 / u : 1.0;
+    if (d < 0) return;
+    double& u = lu[(size_t)d * Pt.n + i];
+    u = (u != 0.0) ? 1.0 / u : 1.0;
+}
+
+// 1 / u_ii of a finished row.
+__device__ __forceinline__ double pivot_inv(const IluPattern& Pt, const double* lu, int i) {
+    const int d = Pt.dslot(i);
+    return d >= 0 ? lu[(size_t)d * Pt.n + i] : 1.0;
 }
 
 // In-place ILU(0) of the group's staged values, level by level.
-__device__ __forceinline__ void ilu_factor_packed(const IluPattern& Pt, double* lu, double* udinv,
-                                                  const Team& tm) {
+__device__ __forceinline__ void ilu_factor_packed(const IluPattern& Pt, double* lu, const Team& tm) {
     const int n = Pt.n;
     for (int t = Pt.slevL[0] + tm.tid; t < Pt.slevL[1]; t += tm.nt) {  // rows without a lower part
         const int i = Pt.srowsL[t];
-        udinv[i] = pivot_inverse(Pt, lu, i);
+        invert_pivot(Pt, lu, i);
     }
     __syncwarp();
     for (int l = 1; l < Pt.nlevL; ++l) {
@@ -129,7 +138,7 @@ __device__ __forceinline__ void ilu_factor_packed(const IluPattern& Pt, double* 
             for (int e = 0; e < len; ++e) {
                 const int kk = Pt.col(e, i);
                 if (kk >= i) break;
-                const double lik = lu[(size_t)e * n + i] * udinv[kk];
+                const double lik = lu[(size_t)e * n + i] * pivot_inv(Pt, lu, kk);
                 lu[(size_t)e * n + i] = lik;
                 const int lenk = Pt.len(kk);
                 int f = 0;
@@ -140,15 +149,15 @@ __device__ __forceinline__ void ilu_factor_packed(const IluPattern& Pt, double* 
                         lu[(size_t)g * n + i] = fma(-lik, lu[(size_t)f * n + kk], lu[(size_t)g * n + i]);
                 }
             }
-            udinv[i] = pivot_inverse(Pt, lu, i);
+            invert_pivot(Pt, lu, i);
         }
         __syncwarp();
     }
 }
 
 // buf = U^-1 L^-1 buf, in place, by the group.
-__device__ __forceinline__ void ilu_apply_packed(const IluPattern& Pt, const double* lu, const double* udinv,
-                                                 double* buf, const Team& tm) {
+__device__ __forceinline__ void ilu_apply_packed(const IluPattern& Pt, const double* lu, double* buf,
+                                                 const Team& tm) {
     const int n = Pt.n;
     for (int l = 1; l < Pt.nlevL; ++l) {
         for (int t = Pt.slevL[l] + tm.tid; t < Pt.slevL[l + 1]; t += tm.nt) {
@@ -173,7 +182,7 @@ __device__ __forceinline__ void ilu_apply_packed(const IluPattern& Pt, const dou
                 if (j <= i) break;
                 sum = fma(-lu[(size_t)e * n + i], buf[j], sum);
             }
-            buf[i] = sum * udinv[i];
+            buf[i] = sum * pivot_inv(Pt, lu, i);
         }
         __syncwarp();
     }
@@ -205,7 +214,7 @@ __device__ __forceinline__ double ilu_packed_residual(const IluPattern& Pt, cons
 // Right-preconditioned BiCGSTAB, M = (L U)^-1, for one group's system.
 template <int L, int R>
 __device__ __forceinline__ void bicgstab_ilu_packed_system(const IluPattern& Pt, const double* vals,
-                                                           const double* lu, const double* udinv,
+                                                           const double* lu,
                                                            const SysIO& io, bool valid, const SolveCfg& C,
                                                            const TeamSmem& sm, const Team& tm) {
     const int n = io.n;
@@ -270,7 +279,7 @@ __device__ __forceinline__ void bicgstab_ilu_packed_system(const IluPattern& Pt,
         for (int q = 0; q < R; ++q) p[q] = fma(beta, fma(-omega, v[q], p[q]), r[q]);
         put(sm.xa, p, tm, n);
         __syncwarp();
-        ilu_apply_packed(Pt, lu, udinv, sm.xa, tm);  // xa = p^
+        ilu_apply_packed(Pt, lu, sm.xa, tm);  // xa = p^
         spmv_gather<R>(Pt, vals, sm.xa, v, tm);
         double s1[1] = {pdot(rh, v)};
         group_sum<L>(s1, tm.lane);
@@ -289,7 +298,7 @@ __device__ __forceinline__ void bicgstab_ilu_packed_system(const IluPattern& Pt,
         for (int q = 0; q < R; ++q) r[q] = fma(-alpha, v[q], r[q]);  // r holds s
         put(sm.xb, r, tm, n);
         __syncwarp();
-        ilu_apply_packed(Pt, lu, udinv, sm.xb, tm);  // xb = s^
+        ilu_apply_packed(Pt, lu, sm.xb, tm);  // xb = s^
         spmv_gather<R>(Pt, vals, sm.xb, t, tm);
         double s3[3] = {pdot(r, r), pdot(t, t), pdot(t, r)};
         group_sum<L>(s3, tm.lane);
@@ -398,8 +407,8 @@ __device__ __forceinline__ void bicgstab_ilu_packed_system(const IluPattern& Pt,
 }
 
 // One warp per block, 32 / L systems per warp; shared memory per group of
-// P.slice bytes: xa [n_pad] | xb [n_pad] | lu at P.stage_off | udinv after
-// lu; after the 32 / L slices, the block's copy of the pattern.
+// P.slice bytes: xa [n_pad] | xb [n_pad] | lu at P.stage_off; after the
+// 32 / L slices, the block's copy of the pattern.
 template <int L, int R>
 __global__ void __launch_bounds__(32, packed_cg_min_blocks(R))
     bicgstab_ilu_packed_kernel(const SolveParams P, const int* sched) {
@@ -424,7 +433,6 @@ __global__ void __launch_bounds__(32, packed_cg_min_blocks(R))
     sm.extra = nullptr;
     double* lu = reinterpret_cast<double*>(slice + P.stage_off);
     const size_t cells = (size_t)P.xk * P.n;
-    double* udinv = lu + ((cells + 1) & ~(size_t)1);
     IluPattern Pt;
     Pt.xcols = P.xcols;
     Pt.xsrc = P.xsrc;
@@ -448,8 +456,8 @@ __global__ void __launch_bounds__(32, packed_cg_min_blocks(R))
         }
         return;
     }
-    ilu_factor_packed(Pt, lu, udinv, tm);
-    bicgstab_ilu_packed_system<L, R>(Pt, vals, lu, udinv, io, valid, solve_cfg(P, sys), sm, tm);
+    ilu_factor_packed(Pt, lu, tm);
+    bicgstab_ilu_packed_system<L, R>(Pt, vals, lu, io, valid, solve_cfg(P, sys), sm, tm);
 }
 
 }  // namespace bbs
