@@ -54,16 +54,12 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 # its own launch by systems (traffic is the compulsory bytes, which grow in
 # proportion). An entry is removed when its kernel changes.
 #   bicgstab_packed_kernel: profiles/bicgstab_packed_kernel_stencil2d5_n144.md
-#   cg_packed_kernel, gmres_packed_kernel, bicgstab_ilu_packed_kernel:
-#                           profiles/packed_cg_gmres_ilu_stencil2d5_n144.md
 #   bicgstab_folded_kernel: profiles/bicgstab_folded_kernel_stencil2d5_n144.md
 #   refine_kernel:          profiles/refine_kernel_stencil2d9_n1024.md
 #   varsize_kernel:         profiles/varsize_kernel_uneven_n16-1024.md (first
 #                           20,000 systems of the uneven batch; per-system
 #                           bytes vary with n, so the scaling is approximate)
-TRAFFIC = {"bicgstab_packed_kernel": (135.8e6, 16384),
-           "cg_packed_kernel": (133.7e6, 16384),
-           "gmres_packed_kernel": (338.5e6, 16384),
+TRAFFIC = {"bicgstab_packed_kernel": (134.9e6, 16384),
            "bicgstab_folded_kernel": (280.8e6, 32768),
            "refine_kernel": (545.0e6, 4096),
            "varsize_kernel": (332.9e6, 20000)}

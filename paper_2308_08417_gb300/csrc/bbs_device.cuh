@@ -176,9 +176,17 @@ __device__ __forceinline__ void spmv_staged(const Mat<V>& A, const V* __restrict
                 if (j < len) sum = fma(T(as[e0 + j]), xs[ldg(A.cols + e0 + j)], sum);
         } else if (row < A.n) {
             if constexpr (FMT == FMT_ELL) {
-                for (int j = 0; j < A.k; ++j) {
-                    const int col = ldg(A.cols + (size_t)j * A.n + row);
-                    if (col >= 0) sum = fma(T(as[(size_t)j * A.n + row]), xs[col], sum);
+                if constexpr (sizeof(T) == 8) {  // FP64: unrolled slots overlap their loads
+#pragma unroll 3
+                    for (int j = 0; j < A.k; ++j) {
+                        const int col = ldg(A.cols + (size_t)j * A.n + row);
+                        if (col >= 0) sum = fma(T(as[(size_t)j * A.n + row]), xs[col], sum);
+                    }
+                } else {
+                    for (int j = 0; j < A.k; ++j) {
+                        const int col = ldg(A.cols + (size_t)j * A.n + row);
+                        if (col >= 0) sum = fma(T(as[(size_t)j * A.n + row]), xs[col], sum);
+                    }
                 }
             } else {
                 const V* a = as + (size_t)row * A.n;
