@@ -557,7 +557,7 @@ def extras(bbs, torch, dev, stream, mhz):
             kr = Uniform(bbs, torch, dev, wl, "csr", dict(solver=solver), f"{solver}_{wl.name}")
             tot, ms, _ = time_steps(kr, torch, stream, 5, 2)
             out[solver] = {"workload": kr.label, "value": kr.num_batch * 5 / (tot / 1e3), "unit": "systems/s",
-                           "launch": kr.launch, "iterations": kr.summary()}
+                           "launch": kr.launch, "iterations": kr.summary(), "roofline": roofline(kr, ms, mhz)}
             del kr
         except Exception as e:
             out[solver] = {"error": repr(e)}
@@ -565,7 +565,8 @@ def extras(bbs, torch, dev, stream, mhz):
         il = Uniform(bbs, torch, dev, W.plain_at_scale(), "csr", dict(precond="ilu0"), "ilu0")
         tot, ms, _ = time_steps(il, torch, stream, 5, 2)
         out["ilu0"] = {"workload": il.wl.name, "value": il.num_batch * 5 / (tot / 1e3),
-                       "unit": "systems/s", "iterations": il.summary(),
+                       "unit": "systems/s", "iterations": il.summary(), "launch": il.launch,
+                       "roofline": roofline(il, ms, mhz),
                        "note": "BiCGSTAB + ILU(0) (level-scheduled factorisation and triangular solves)"}
         del il
     except Exception as e:
