@@ -362,10 +362,10 @@ __device__ __forceinline__ void cg_packed_system(const PackedOp<FMT, R>& op, con
         if (!__any_sync(kFull, active)) break;
         if (active) {
             iters = it;
-            if (!finite(rho)) {
+            if (!finite64(rho)) {
                 status = ST_NAN;
                 active = false;
-            } else if (rho == 0.0) {
+            } else if (zero64(rho)) {
                 status = ST_BREAKDOWN;
                 active = false;
             }
@@ -377,10 +377,10 @@ __device__ __forceinline__ void cg_packed_system(const PackedOp<FMT, R>& op, con
         group_sum<L>(s1, tm.lane);
         const double pt = s1[0];
         if (active) {
-            if (!finite(pt)) {
+            if (!finite64(pt)) {
                 status = ST_NAN;
                 active = false;
-            } else if (pt == 0.0) {
+            } else if (zero64(pt)) {
                 status = ST_BREAKDOWN;
                 active = false;
             }
@@ -392,20 +392,26 @@ __device__ __forceinline__ void cg_packed_system(const PackedOp<FMT, R>& op, con
             const double nx = fma(alpha, p[q], x[q]);
             if (active) x[q] = nx;
             r[q] = fma(-alpha, t[q], r[q]);
+            t[q] = dinv[q] * r[q];  // z = M r, held in t until p is updated
             s2[0] = fma(r[q], r[q], s2[0]);
-            s2[1] = fma(r[q], dinv[q] * r[q], s2[1]);
+            s2[1] = fma(r[q], t[q], s2[1]);
         }
         group_sum<L>(s2, tm.lane);
         bool cand = false;
         if (active) {
             rr = s2[0];
-            if (!finite(rr)) {
+            if (!finite64(rr)) {
                 status = ST_NAN;
                 active = false;
             } else {
-                cand = rr <= tau2;
+                cand = le_nonneg64(rr, tau2);
             }
         }
+        // p = z + (rho_new / rho) p now, before a confirmation may reuse t;
+        // a restart below replaces p with M r_true.
+        const double ratio = s2[1] / rho;
+#pragma unroll
+        for (int q = 0; q < R; ++q) p[q] = fma(ratio, p[q], t[q]);
         bool restarted = false;
         if (__any_sync(kFull, cand)) {
             put(sm.xa, x, tm, n);
@@ -443,12 +449,7 @@ __device__ __forceinline__ void cg_packed_system(const PackedOp<FMT, R>& op, con
                 }
             }
         }
-        const double ratio = s2[1] / rho;
-        if (!restarted) {
-#pragma unroll
-            for (int q = 0; q < R; ++q) p[q] = fma(ratio, p[q], dinv[q] * r[q]);
-            if (active) rho = s2[1];
-        }
+        if (!restarted && active) rho = s2[1];
     }
     if (active) status = ST_MAX_ITER;
     const bool need = valid && special == 0 && !have_res;
@@ -587,7 +588,7 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
                 }
                 double h[1] = {pdot(w, vr)};
                 group_sum<L>(h, tm.lane);
-                bad |= !finite(h[0]);
+                bad |= !finite64(h[0]);
 #pragma unroll
                 for (int q = 0; q < R; ++q) w[q] = fma(-h[0], vr[q], w[q]);
                 if (cyc && lead) H[i * m + j] = h[0];
@@ -595,7 +596,7 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
             double hw[1] = {pdot(w, w)};
             group_sum<L>(hw, tm.lane);
             const double hn = sqrt(hw[0]);
-            bad |= !finite(hn);
+            bad |= !finite64(hn);
             if (cyc && bad) {
                 status = ST_NAN;
                 active = false;
