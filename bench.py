@@ -223,14 +223,17 @@ class Uniform:
         bbs, torch = self.bbs, self.torch
         hA = bbs.DeviceBatch.from_batch(self.A, "cpu", pin=True)
         hb = torch.as_tensor(self.wl.b).pin_memory()
-        hx0 = torch.as_tensor(self.wl.x0).pin_memory()
-        hx = hx0.clone().pin_memory()
+        hx0 = torch.as_tensor(self.wl.x0)
+        # x is in/out: every call gets its own pinned copy of x0, made before
+        # the timed region (restoring one buffer on the host would time a
+        # host memcpy of the whole x that is not part of the call)
+        hxs = [hx0.clone().pin_memory() for _ in range(reps + 1)]
+        hx = hxs[0]
         hlog = bbs.Log.empty(self.num_batch, device="cpu", pin=True, inner=self.mixed)
-        self.h.solve_host(hA, hb, hx, self.opts, hlog)
+        self.h.solve_host(hA, hb, hxs[reps], self.opts, hlog)
         t0 = time.perf_counter()
-        for _ in range(reps):
-            hx.copy_(hx0)
-            self.h.solve_host(hA, hb, hx, self.opts, hlog)
+        for i in range(reps):
+            self.h.solve_host(hA, hb, hxs[i], self.opts, hlog)
         dt = (time.perf_counter() - t0) / reps
         h2d = (hA.values.numel() * 8 + (hA.row_ptrs.numel() * 4 if hA.row_ptrs is not None else 0)
                + (hA.col_idxs.numel() * 4 if hA.col_idxs is not None else 0) + 2 * hb.numel() * 8)

@@ -208,10 +208,12 @@ bbs_status bbs_solve(bbs_handle *handle, const bbs_batch_matrix *A, const double
  * x0, out: x) and log are HOST pointers. The library copies the inputs to
  * device buffers owned by the handle, solves, copies x and the log back and
  * waits for completion. The batch goes in chunks of about 128 MB of input
- * (at most 8, at least 2,048 systems each) that alternate between two
- * streams, so that one chunk's copies overlap another's solve (page-locked
- * host memory lets them overlap); results are the same as one bbs_solve of
- * the whole batch. */
+ * (at least 2,048 systems each), led by a quarter and a half chunk. The
+ * inputs are copied in on a stream of their own, chunk after chunk; each
+ * chunk's solve waits for its copy only, and the solves and the copies out
+ * alternate between two more streams, so copies overlap solves and
+ * consecutive solves overlap each other (with page-locked host memory);
+ * results are the same as one bbs_solve of the whole batch. */
 bbs_status bbs_solve_host(bbs_handle *handle, const bbs_batch_matrix *A_host,
                           const double *b_host, double *x_host, const bbs_options *opts,
                           const bbs_log *log_host);

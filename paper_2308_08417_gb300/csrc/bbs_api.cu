@@ -21,11 +21,13 @@ struct bbs_handle {
     int sms = 0;
     int max_smem_optin = 0;
     int max_threads = 1024;
-    // bbs_solve_host: two streams, so that one chunk's copies overlap the
-    // other's solve, and an event that orders the pattern copy before both
+    // bbs_solve_host: the inputs go in on `copy_in`, chunk after chunk, each
+    // chunk signalling `chunk_in[c]`; the solves and the copies out alternate
+    // between `stream` and `stream2`, so consecutive solves overlap
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;
-    cudaEvent_t pattern_ready = nullptr;
+    cudaStream_t copy_in = nullptr;
+    cudaEvent_t chunk_in[16] = {nullptr};
     // device buffers owned for bbs_solve_host (grow only)
     void* buf[12] = {nullptr};
     size_t cap[12] = {0};
@@ -370,13 +372,14 @@ bbs_status bbs_create(bbs_handle** handle, int device) {
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&h->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     cudaDeviceGetAttribute(&h->max_threads, cudaDevAttrMaxThreadsPerBlock, device);
-    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&h->pattern_ready, cudaEventDisableTiming)) != cudaSuccess) {
-        if (h->stream) cudaStreamDestroy(h->stream);
-        if (h->stream2) cudaStreamDestroy(h->stream2);
-        delete h;
-        return cuda_fail(e, "cudaStreamCreate");
+    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) == cudaSuccess &&
+        (e = cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking)) == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking);
+    for (cudaEvent_t& ev : h->chunk_in)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        bbs_destroy(h);
+        return cuda_fail(e, "stream or event creation");
     }
     *handle = h;
     return BBS_OK;
@@ -389,7 +392,9 @@ bbs_status bbs_destroy(bbs_handle* h) {
         if (h->buf[i]) cudaFree(h->buf[i]);
     if (h->stream) cudaStreamDestroy(h->stream);
     if (h->stream2) cudaStreamDestroy(h->stream2);
-    if (h->pattern_ready) cudaEventDestroy(h->pattern_ready);
+    if (h->copy_in) cudaStreamDestroy(h->copy_in);
+    for (cudaEvent_t ev : h->chunk_in)
+        if (ev) cudaEventDestroy(ev);
     delete h;
     return BBS_OK;
 }
@@ -586,12 +591,12 @@ static bbs_status ensure(bbs_handle* h, int slot, size_t bytes, void** out) {
 }
 
 // bbs_solve_host cuts a batch into chunks of about kHostChunkBytes of input
-// (at most kHostChunks, at least kHostMinChunk systems each) that alternate
-// between the handle's two streams, so the copies of one chunk overlap the
-// solve of the other. Measured on GB300: 65,536 systems of 144 rows (503 MB)
-// run best in 4 chunks (8 chunks leave each solve a partial last wave);
-// 16,384 systems of 1,024 rows (1.5 GB) in 8. Per-system results do not
-// depend on the chunking.
+// (at most kHostChunks of that size, at least kHostMinChunk systems each),
+// led by a ramp of a quarter and a half chunk so that the first solve starts
+// after a short copy. The inputs stream in on their own stream, chunk after
+// chunk, never waiting for a solve; each solve waits only for its chunk and
+// alternates with the next between two streams, so their partial last waves
+// overlap. Per-system results do not depend on the chunking.
 constexpr size_t kHostChunkBytes = 128u << 20;
 constexpr size_t kHostMinChunk = 2048;
 constexpr size_t kHostChunks = 8;
@@ -624,7 +629,14 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
     const size_t in_bytes = B * (vps * (Ah->values_f32 ? 12 : 8) + 2 * n * 8);
     const size_t want = std::min(kHostChunks, std::max<size_t>(1, (in_bytes + kHostChunkBytes - 1) / kHostChunkBytes));
     const size_t chunk = std::min(B, std::max(kHostMinChunk, (B + want - 1) / want));
-    const size_t nchunks = (B + chunk - 1) / chunk;
+    // at most 2 + kHostChunks chunks: the ramp, then chunks of `chunk`
+    size_t first[16], count[16], nchunks = 0;
+    for (size_t c0 = 0; c0 < B; c0 += count[nchunks++]) {
+        if (nchunks == 16) return fail(BBS_ERR_UNSUPPORTED, "host batch cut into too many chunks");
+        const size_t ramp = nchunks == 0 ? chunk / 4 : nchunks == 1 ? chunk / 2 : chunk;
+        first[nchunks] = c0;
+        count[nchunks] = std::min(B - c0, std::max(kHostMinChunk, ramp));
+    }
     bbs_batch_matrix Ad = *Ah;
     Ad.row_ptrs = static_cast<const int32_t*>(d_rp);
     Ad.col_idxs = static_cast<const int32_t*>(d_ci);
@@ -640,24 +652,25 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
     cudaError_t e = cudaSuccess;
 #define BBS_CP(dst, src, bytes, kind, st)                                          \
     if ((bytes) > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, kind, st)
-    BBS_CP(d_rp, Ah->row_ptrs, rp_bytes, cudaMemcpyHostToDevice, streams[0]);
-    BBS_CP(d_ci, Ah->col_idxs, ci_bytes, cudaMemcpyHostToDevice, streams[0]);
-    if (e == cudaSuccess) e = cudaEventRecord(h->pattern_ready, streams[0]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(streams[1], h->pattern_ready, 0);
+    BBS_CP(d_rp, Ah->row_ptrs, rp_bytes, cudaMemcpyHostToDevice, h->copy_in);
+    BBS_CP(d_ci, Ah->col_idxs, ci_bytes, cudaMemcpyHostToDevice, h->copy_in);
     if (e != cudaSuccess) return cuda_fail(e, "pattern copy");
     for (size_t c = 0; c < nchunks; ++c) {
         cudaStream_t st = streams[c & 1];
-        const size_t c0 = c * chunk, cb = std::min(chunk, B - c0);
+        const size_t c0 = first[c], cb = count[c];
         char* v = static_cast<char*>(d_v) + c0 * vps * 8;
         char* v32 = Ah->values_f32 ? static_cast<char*>(d_v32) + c0 * vps * 4 : nullptr;
         double* bd = static_cast<double*>(d_b) + c0 * n;
         double* xd = static_cast<double*>(d_x) + c0 * n;
-        BBS_CP(v, reinterpret_cast<const char*>(Ah->values) + c0 * vps * 8, cb * vps * 8, cudaMemcpyHostToDevice, st);
+        BBS_CP(v, reinterpret_cast<const char*>(Ah->values) + c0 * vps * 8, cb * vps * 8, cudaMemcpyHostToDevice,
+               h->copy_in);
         if (Ah->values_f32)
             BBS_CP(v32, reinterpret_cast<const char*>(Ah->values_f32) + c0 * vps * 4, cb * vps * 4,
-                   cudaMemcpyHostToDevice, st);
-        BBS_CP(bd, b_host + c0 * n, cb * n * 8, cudaMemcpyHostToDevice, st);
-        BBS_CP(xd, x_host + c0 * n, cb * n * 8, cudaMemcpyHostToDevice, st);
+                   cudaMemcpyHostToDevice, h->copy_in);
+        BBS_CP(bd, b_host + c0 * n, cb * n * 8, cudaMemcpyHostToDevice, h->copy_in);
+        BBS_CP(xd, x_host + c0 * n, cb * n * 8, cudaMemcpyHostToDevice, h->copy_in);
+        if (e == cudaSuccess) e = cudaEventRecord(h->chunk_in[c], h->copy_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->chunk_in[c], 0);
         if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
         bbs_batch_matrix Ac = Ad;
         Ac.num_batch = (int32_t)cb;
@@ -674,7 +687,7 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
         if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     }
 #undef BBS_CP
-    for (cudaStream_t st : streams)
+    for (cudaStream_t st : {h->copy_in, h->stream, h->stream2})
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "solve");
     return BBS_OK;
 }
