@@ -595,7 +595,10 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
             }
             double hw[1] = {pdot(w, w)};
             group_sum<L>(hw, tm.lane);
-            const double hn = sqrt(hw[0]);
+            // h_{j+1,j} = ||w|| and its reciprocal from one rsqrt (every lane
+            // runs this: cheaper than a square root and a division)
+            const double hinv = rsqrt(hw[0]);
+            const double hn = __double_as_longlong(hw[0]) > 0 ? hw[0] * hinv : hw[0];
             bad |= !finite64(hn);
             if (cyc && bad) {
                 status = ST_NAN;
@@ -617,8 +620,9 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
                     c0 = j;
                     c1 = 1;
                 } else {
-                    cs[j] = a / denom;
-                    sn[j] = hn / denom;
+                    const double dinv = 1.0 / denom;
+                    cs[j] = a * dinv;
+                    sn[j] = hn * dinv;
                     H[j * m + j] = denom;
                     H[(j + 1) * m + j] = 0.0;
                     g[j + 1] = -sn[j] * g[j];
@@ -638,7 +642,6 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
             __syncwarp();  // ctl is rewritten in the next step
             if (cyc && (singular || estimate_ok || it >= C.max_iters)) cyc = false;
             if (cyc) {
-                const double hinv = 1.0 / hn;
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     const int row = tm.row(q);
