@@ -50,25 +50,40 @@ NUM_SMS = 152
 HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 
 # dram bytes (read + write) of one launch of a kernel from an ncu capture of
-# it, with the number of systems that launch solved; the bench scales them to
-# its own launch by systems (traffic is the compulsory bytes, which grow in
-# proportion). An entry is removed when its kernel changes.
-#   bicgstab_packed_kernel: profiles/bicgstab_packed_kernel_stencil2d5_n144.md
-#   bicgstab_folded_kernel: profiles/bicgstab_folded_kernel_stencil2d5_n144.md
-#   refine_kernel:          profiles/refine_kernel_stencil2d9_n1024.md
-#   varsize_kernel:         profiles/varsize_kernel_uneven_n16-1024.md (first
-#                           20,000 systems of the uneven batch; per-system
-#                           bytes vary with n, so the scaling is approximate)
-TRAFFIC = {"bicgstab_packed_kernel": (134.9e6, 16384),
-           "bicgstab_folded_kernel": (280.8e6, 32768),
-           "refine_kernel": (545.0e6, 4096),
-           "varsize_kernel": (332.9e6, 20000)}
+# it, with the number of systems that launch solved, keyed by kernel and
+# workload shape (the workload label without its batch size); the bench
+# scales them to its own launch of the same shape by systems (traffic is the
+# compulsory bytes, which grow in proportion). A kernel run on a workload
+# without a capture reports null, and an entry is removed when its kernel
+# changes.
+#   bicgstab_packed_kernel:     profiles/bicgstab_packed_kernel_stencil2d5_n144.md
+#   bicgstab_folded_kernel:     profiles/bicgstab_folded_kernel_stencil2d5_n144.md
+#   cg_packed_kernel,
+#   bicgstab_ilu_packed_kernel: profiles/packed_cg_gmres_ilu_stencil2d5_n144.md
+#   refine_kernel:              profiles/refine_kernel_stencil2d9_n1024.md
+#   varsize_kernel:             profiles/varsize_kernel_uneven_n16-1024.md (first
+#                               20,000 systems of the uneven batch; per-system
+#                               bytes vary with n, so the scaling is approximate)
+TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (134.9e6, 16384),
+           ("bicgstab_folded_kernel", "stencil2d5_12x12"): (280.8e6, 32768),
+           ("cg_packed_kernel", "sym_stencil2d5_12x12_cg+jacobi"): (133.05e6, 16384),
+           ("bicgstab_ilu_packed_kernel", "stencil2d5_12x12_bicgstab+ilu0"): (135.03e6, 16384),
+           ("refine_kernel", "stencil2d9_32x32"): (545.0e6, 4096),
+           ("varsize_kernel", "uneven_n16-1024"): (332.9e6, 20000)}
 
 
-def traffic_bytes(kernel, systems):
-    if kernel not in TRAFFIC:
+def workload_shape(label):
+    """A workload label without its batch size (`_B<count>`)."""
+    import re
+
+    return re.sub(r"_B[0-9]+", "", label)
+
+
+def traffic_bytes(kernel, label, systems):
+    key = (kernel, workload_shape(label))
+    if key not in TRAFFIC:
         return None
-    b, s = TRAFFIC[kernel]
+    b, s = TRAFFIC[key]
     return b / s * systems
 
 
@@ -507,7 +522,7 @@ def roofline(r, solve_ms, mhz):
     peak = per_clk * NUM_SMS * mhz * 1e6 / 1e12
     achieved = flops / avg_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic_bytes(r.kernel, r.num_batch), "kernel": r.kernel,
+            "frac": achieved / peak, "traffic": traffic_bytes(r.kernel, r.label, r.num_batch), "kernel": r.kernel,
             "arith": arith,
             "peak_source": f"{arith.upper()} {per_clk:g} FLOP/clk/SM x {NUM_SMS} SMs x median SM clock {mhz:.0f} MHz"}
 
@@ -545,8 +560,8 @@ def extras(bbs, torch, dev, stream, mhz):
     except Exception as e:  # report, do not hide
         out["mixed"] = {"error": repr(e)}
     try:  # the same headline batch with one system per warp (no packing)
-        ow = Uniform(bbs, torch, dev, W.plain_at_scale(), "csr", dict(threads_per_system=32),
-                     "one_system_per_warp")
+        wl = W.plain_at_scale()
+        ow = Uniform(bbs, torch, dev, wl, "csr", dict(threads_per_system=32), wl.name)
         tot, ms, _ = time_steps(ow, torch, stream, 5, 2)
         out["one_system_per_warp"] = {"workload": ow.wl.name, "value": ow.num_batch * 5 / (tot / 1e3),
                                       "unit": "systems/s", "launch": ow.launch, "iterations": ow.summary(),
@@ -557,7 +572,7 @@ def extras(bbs, torch, dev, stream, mhz):
     for solver in ("cg", "gmres"):  # the other Krylov solvers on the headline shape
         try:
             wl = W.plain_at_scale(symmetric=(solver == "cg"))
-            kr = Uniform(bbs, torch, dev, wl, "csr", dict(solver=solver), f"{solver}_{wl.name}")
+            kr = Uniform(bbs, torch, dev, wl, "csr", dict(solver=solver), f"{wl.name}_{solver}+jacobi")
             tot, ms, _ = time_steps(kr, torch, stream, 5, 2)
             out[solver] = {"workload": kr.label, "value": kr.num_batch * 5 / (tot / 1e3), "unit": "systems/s",
                            "launch": kr.launch, "iterations": kr.summary(), "roofline": roofline(kr, ms, mhz)}
@@ -565,9 +580,10 @@ def extras(bbs, torch, dev, stream, mhz):
         except Exception as e:
             out[solver] = {"error": repr(e)}
     try:  # the same headline batch with the batched ILU(0) preconditioner
-        il = Uniform(bbs, torch, dev, W.plain_at_scale(), "csr", dict(precond="ilu0"), "ilu0")
+        wl = W.plain_at_scale()
+        il = Uniform(bbs, torch, dev, wl, "csr", dict(precond="ilu0"), f"{wl.name}_bicgstab+ilu0")
         tot, ms, _ = time_steps(il, torch, stream, 5, 2)
-        out["ilu0"] = {"workload": il.wl.name, "value": il.num_batch * 5 / (tot / 1e3),
+        out["ilu0"] = {"workload": il.label, "value": il.num_batch * 5 / (tot / 1e3),
                        "unit": "systems/s", "iterations": il.summary(), "launch": il.launch,
                        "roofline": roofline(il, ms, mhz),
                        "note": "BiCGSTAB + ILU(0) (level-scheduled factorisation and triangular solves)"}
