@@ -74,8 +74,11 @@ typedef enum {
  *          padding value 0; row_ptrs unused (may be NULL)
  *   DENSE: values [num_batch * n * n] row-major; row_ptrs/col_idxs unused
  * System i's values start at values + i * (nnz | ell_k*n | n*n).
- * values_f32: optional FP32 copy in the same layout, used by the mixed mode;
- * NULL makes the library convert into the workspace inside the call. */
+ * values_f32: optional FP32 copy in the same layout, used by the mixed mode.
+ * With NULL, each block rounds its system's FP64 values to FP32 (to nearest)
+ * as it stages them into shared memory; values too large to stage are
+ * converted into the workspace inside the call instead. Either way the
+ * results equal those with a copy rounded to nearest. */
 typedef struct {
     int32_t fmt; /* bbs_format */
     int32_t num_batch;
@@ -149,7 +152,7 @@ bbs_status bbs_destroy(bbs_handle *handle);
 
 /* Bytes of DEVICE workspace bbs_solve needs for this problem (0 is possible).
  * Workspace use: the FP32 copy of the values in mixed mode when values_f32
- * is NULL, the GMRES Krylov basis (always for packed systems, else when it
+ * is NULL and the values are not staged in shared memory, the GMRES Krylov basis (always for packed systems, else when it
  * does not fit in shared memory: (restart + 1) * n_pad doubles per system), the
  * ILU(0) level schedule of the shared pattern, and for packed systems on CSR
  * the pattern as an ELL column table (2 * ell_k * n int32 + 256 bytes). */

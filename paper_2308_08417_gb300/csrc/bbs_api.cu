@@ -284,7 +284,9 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
     p->stage = stage;
     p->stage_off = base;
     p->smem = base + (stage ? stage_bytes : 0);
-    if (mixed && A->values_f32 == nullptr) p->ws_f32 = align_up(vps * 4 * (size_t)A->num_batch, 256);
+    // without the caller's FP32 copy, staged values are rounded as the kernel
+    // stages them; only unstaged values need a converted copy in the workspace
+    if (mixed && A->values_f32 == nullptr && !stage) p->ws_f32 = align_up(vps * 4 * (size_t)A->num_batch, 256);
     return BBS_OK;
 }
 

@@ -88,6 +88,24 @@ __device__ __forceinline__ int inner_bicgstab32(const Op<FMT, R, float, float>& 
     return max_inner;
 }
 
+// Copy `count` FP64 values to shared memory rounded to FP32 (to nearest, as
+// convert_f32_kernel rounds), with 16-byte loads when the source allows.
+__device__ __forceinline__ void stage_values_rounded(const double* __restrict__ g, float* __restrict__ s,
+                                                     size_t count, const Team& tm) {
+    size_t i = 0;
+    if ((reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+        const size_t nv = count / 2;
+        const double2* gv = reinterpret_cast<const double2*>(g);
+        float2* sv = reinterpret_cast<float2*>(s);
+        for (size_t j = tm.tid; j < nv; j += tm.nt) {
+            const double2 v = __ldg(gv + j);
+            sv[j] = make_float2((float)v.x, (float)v.y);
+        }
+        i = nv * 2;
+    }
+    for (size_t j = i + tm.tid; j < count; j += tm.nt) s[j] = (float)ldg(g + j);
+}
+
 // Shared memory: red64[256] | xd[n_pad] (FP64) | red32[256] | xa[n_pad] |
 // xb[n_pad] (FP32) | staged FP32 values (optional)
 template <int FMT, int R>
@@ -106,11 +124,17 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const Sol
 
     const Mat<double> A64{P.values + (size_t)sys * P.vps, P.row_ptrs, P.cols, n, P.k};
     const Op<FMT, R, double, double> op64{A64, nullptr};
-    const Mat<float> A32{P.values32 + (size_t)sys * P.vps, P.row_ptrs, P.cols, n, P.k};
+    // Without an FP32 copy (values32 == nullptr, only when the values are
+    // staged) the block rounds the FP64 values to FP32 as it stages them.
+    const bool copy32 = P.values32 != nullptr;
+    const Mat<float> A32{copy32 ? P.values32 + (size_t)sys * P.vps : nullptr, P.row_ptrs, P.cols, n, P.k};
     const float* as = nullptr;
     if (P.stage) {
         float* s = reinterpret_cast<float*>(raw + P.stage_off);
-        stage_values(A32.vals, s, P.vps, tm);
+        if (copy32)
+            stage_values(A32.vals, s, P.vps, tm);
+        else
+            stage_values_rounded(A64.vals, s, P.vps, tm);
         tm.sync();
         as = s;
     }
@@ -119,7 +143,10 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const Sol
     double b[R], x[R], r[R];
     float dinv[R], w[R], d[R];
     load_system<R>(io, b, x, tm);
-    jacobi_setup<FMT, R>(A32, P.precond == 1, dinv, tm);
+    if (copy32)
+        jacobi_setup<FMT, R>(A32, P.precond == 1, dinv, tm);
+    else  // 1 / a_ii in FP32 of the FP32-rounded diagonal, as from a copy
+        jacobi_setup<FMT, R>(A64, P.precond == 1, dinv, tm);
 
     double s0[1] = {pdot(b, b)};
     block_sum(s0, red64, par64, tm);

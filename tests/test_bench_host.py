@@ -23,6 +23,7 @@ def test_workload_shape_drops_only_the_batch_size(bench):
     assert bench.workload_shape("stencil2d5_12x12_B65536") == "stencil2d5_12x12"
     assert bench.workload_shape("sym_stencil2d5_12x12_B16384_cg+jacobi") == "sym_stencil2d5_12x12_cg+jacobi"
     assert bench.workload_shape("uneven_n16-1024_B100000") == "uneven_n16-1024"
+    assert bench.workload_shape("stencil2d5_12x12_B65536[:16384]") == "stencil2d5_12x12"
 
 
 def test_traffic_scales_by_systems_within_a_shape(bench):

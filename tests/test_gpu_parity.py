@@ -146,6 +146,28 @@ def test_mixed_refinement(bbs, handle, given_f32):
     assert (g[4] >= g[1]).all()
 
 
+@pytest.mark.parametrize("fmt", ["ell", "csr"])
+def test_mixed_fp32_rounding_paths_agree(bbs, handle, fmt):
+    """The three ways the FP32 values reach the inner solve give the same
+    bits: the caller's copy (rounded to nearest on the host), rounding while
+    staging into shared memory (no copy, no workspace, one launch), and the
+    library's conversion into the workspace (values not staged)."""
+    wl = W.mixed_precision(96, grid=16)
+    A = wl.matrix(fmt)
+    kw = dict(precision="mixed", inner_tol=3e-3, max_iters=200, max_outer=30)
+    given = gpu_solve(bbs, handle, A, wl.b, values_f32=True, **kw)
+    fused = gpu_solve(bbs, handle, A, wl.b, **kw)
+    unstaged = gpu_solve(bbs, handle, A, wl.b, values_in_smem=-1, **kw)
+    for other in (fused, unstaged):
+        for a, b in zip(given, other):
+            assert np.array_equal(a, b)
+    assert (given[3] == 0).all()
+    dA = bbs.DeviceBatch.from_batch(A, "cuda")
+    info = handle.describe(dA, bbs.bbs_default_options(**kw))
+    assert info["kernel"] == "refine_kernel" and info["staged"] and info["launches"] == 1
+    assert handle.workspace_size(dA, bbs.bbs_default_options(**kw)) == 0
+
+
 # ---------------------------------------------------------- edge cases
 
 def test_edge_cases(bbs, handle):
