@@ -196,7 +196,7 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
             // after the values: the GMRES Hessenberg, rotations, right-hand side,
             // solution and control words
             const size_t mr = (size_t)o->gmres_restart;
-            const size_t extra = gmres ? ((mr + 1) * mr + 2 * mr + (mr + 1) + mr + 2) * 8 : 0;
+            const size_t extra = gmres ? (mr * (mr + 3) / 2 + 2 * mr + (mr + 1) + mr + 2) * 8 : 0;
             const size_t slice = packed_slice(n_pad, vps, L, &off, extra);
             // ILU(0) blocks also hold one copy of the pattern for their groups
             const size_t smem = slice * (size_t)(32 / L) + (ilu ? bbs::ilu_pattern_smem(n, A->ell_k) : 0);

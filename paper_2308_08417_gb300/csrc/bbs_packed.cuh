@@ -494,8 +494,11 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
     const bool jac = C.precond == 1;
     const size_t vs = (size_t)((n + 1) & ~1);
     double* V = C.ws;
+    // H holds the (m + 1) x m Hessenberg column by column, only rows 0..j + 1
+    // of column j: entry (i, j) at j (j + 3) / 2 + i, m (m + 3) / 2 in all
     double* H = ext;
-    double* cs = H + (m + 1) * m;
+    const auto hx = [](int i, int j) { return j * (j + 3) / 2 + i; };
+    double* cs = H + m * (m + 3) / 2;
     double* sn = cs + m;
     double* g = sn + m;
     double* y = g + m + 1;
@@ -591,7 +594,7 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
                 bad |= !finite64(h[0]);
 #pragma unroll
                 for (int q = 0; q < R; ++q) w[q] = fma(-h[0], vr[q], w[q]);
-                if (cyc && lead) H[i * m + j] = h[0];
+                if (cyc && lead) H[hx(i, j)] = h[0];
             }
             double hw[1] = {pdot(w, w)};
             group_sum<L>(hw, tm.lane);
@@ -607,13 +610,13 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
                 nan_exit = true;
             }
             if (cyc && lead) {
-                H[(j + 1) * m + j] = hn;
+                H[hx(j + 1, j)] = hn;
                 for (int i = 0; i < j; ++i) {
-                    const double a = H[i * m + j], c = H[(i + 1) * m + j];
-                    H[i * m + j] = cs[i] * a + sn[i] * c;
-                    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+                    const double a = H[hx(i, j)], c = H[hx(i + 1, j)];
+                    H[hx(i, j)] = cs[i] * a + sn[i] * c;
+                    H[hx(i + 1, j)] = -sn[i] * a + cs[i] * c;
                 }
-                const double a = H[j * m + j];
+                const double a = H[hx(j, j)];
                 const double denom = sqrt(a * a + hn * hn);
                 int c0, c1 = 0, c2 = 0;
                 if (denom == 0.0) {
@@ -623,8 +626,8 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
                     const double dinv = 1.0 / denom;
                     cs[j] = a * dinv;
                     sn[j] = hn * dinv;
-                    H[j * m + j] = denom;
-                    H[(j + 1) * m + j] = 0.0;
+                    H[hx(j, j)] = denom;
+                    H[hx(j + 1, j)] = 0.0;
                     g[j + 1] = -sn[j] * g[j];
                     g[j] = cs[j] * g[j];
                     c0 = j + 1;
@@ -654,8 +657,8 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
         if (upd && lead) {
             for (int i = k - 1; i >= 0; --i) {
                 double sum = g[i];
-                for (int l = i + 1; l < k; ++l) sum -= H[i * m + l] * y[l];
-                y[i] = sum / H[i * m + i];
+                for (int l = i + 1; l < k; ++l) sum -= H[hx(i, l)] * y[l];
+                y[i] = sum / H[hx(i, i)];
             }
         }
         __syncwarp();

@@ -44,7 +44,6 @@ def test_every_table_entry_names_a_workload_the_bench_runs(bench):
         bench.workload_shape(W.plain_at_scale(64).name),
         bench.workload_shape(W.plain_at_scale(64, symmetric=True).name + "_cg+jacobi"),
         bench.workload_shape(W.plain_at_scale(64).name + "_bicgstab+ilu0"),
-        bench.workload_shape(W.plain_at_scale(64).name + "_gmres+jacobi"),
         bench.workload_shape(W.mixed_precision(8, grid=32).name),
         bench.workload_shape(W.uneven(64).name),
     }
