@@ -58,8 +58,7 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 # changes.
 #   bicgstab_packed_kernel:     profiles/bicgstab_packed_kernel_stencil2d5_n144.md
 #   bicgstab_folded_kernel:     profiles/bicgstab_folded_kernel_stencil2d5_n144.md
-#   cg_packed_kernel,
-#   bicgstab_ilu_packed_kernel: profiles/packed_cg_gmres_ilu_stencil2d5_n144.md
+#   cg_packed_kernel:           profiles/packed_cg_gmres_ilu_stencil2d5_n144.md
 #   refine_kernel:              profiles/refine_kernel_stencil2d9_n1024.md
 #   varsize_kernel:             profiles/varsize_kernel_uneven_n16-1024.md (first
 #                               20,000 systems of the uneven batch; per-system
@@ -67,7 +66,6 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (134.9e6, 16384),
            ("bicgstab_folded_kernel", "stencil2d5_12x12"): (280.8e6, 32768),
            ("cg_packed_kernel", "sym_stencil2d5_12x12_cg+jacobi"): (133.05e6, 16384),
-           ("bicgstab_ilu_packed_kernel", "stencil2d5_12x12_bicgstab+ilu0"): (135.03e6, 16384),
            ("refine_kernel", "stencil2d9_32x32"): (398.9e6, 4096),
            ("varsize_kernel", "uneven_n16-1024"): (332.9e6, 20000)}
 

@@ -20,11 +20,11 @@ struct IluSchedule {
 __host__ __device__ inline size_t ilu_schedule_ints(int n) { return 2 + 2 * ((size_t)n + 1) + 4 * (size_t)n; }
 
 // Shared-memory bytes of a packed ILU(0) block's copy of the pattern (n <=
-// 160): 16-bit column table [k n] and value map [k n], then 8-bit row lengths
-// [n], diagonal slots [n], lower level pointers [n + 1] and rows [n], upper
-// level pointers [n + 1] and rows [n].
+// 160, nnz < 2^15): 16-bit CSR row starts [n], then 8-bit column table [k n]
+// (255 past the row end), row lengths [n], diagonal slots [n], lower level
+// pointers [n + 1] and rows [n], upper level pointers [n + 1] and rows [n].
 __host__ __device__ inline size_t ilu_pattern_smem(int n, int k) {
-    return (2 * (size_t)k * n * 2 + 6 * (size_t)n + 2 + 15) & ~(size_t)15;
+    return (2 * (size_t)n + (size_t)k * n + 6 * (size_t)n + 2 + 15) & ~(size_t)15;
 }
 
 __device__ __forceinline__ IluSchedule ilu_schedule(const int* sched, int n) {

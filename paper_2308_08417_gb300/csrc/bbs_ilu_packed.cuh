@@ -29,18 +29,17 @@ namespace bbs {
 
 // The pattern as the packed ILU kernels read it. The dependent steps of the
 // factorisation and the triangular solves read it from a block-shared copy
-// in shared memory (n <= 160): the ELL column table (16-bit, -1 past the row
-// end), each row's length and diagonal slot and the level schedule (8-bit);
-// the SpMV also reads the map from slots to CSR values there (16-bit: CSR
-// indices stay below 2^15 as nnz <= n^2 <= 25,600) and gathers the values
-// themselves from global memory.
+// in shared memory: the ELL column table, each row's length and diagonal
+// slot and the level schedule, all 8-bit (n <= 160), and each row's CSR start
+// (16-bit: nnz < 2^15), from which the SpMV finds slot j of row i at CSR
+// entry srp[i] + j and gathers the value from global memory.
 struct IluPattern {
     const int32_t* xcols;  // global
     const int32_t* xsrc;   // global
     int n, k;
     int nlevL, nlevU;
-    const int16_t* scols;  // shared [k n]
-    const int16_t* ssrc;   // shared [k n], -1 past the row end
+    const uint16_t* srp;   // shared [n]: CSR start of each row (slot j of row i is entry srp[i] + j)
+    const uint8_t* scols;  // shared [k n], 255 past the row end
     const uint8_t* slen;   // shared [n]
     const uint8_t* sdslot; // shared [n], 255 without a stored diagonal
     const uint8_t* slevL;  // shared [nlevL + 1]
@@ -48,28 +47,29 @@ struct IluPattern {
     const uint8_t* slevU;  // shared [nlevU + 1]
     const uint8_t* srowsU; // shared [n]
     __device__ __forceinline__ int len(int i) const { return slen[i]; }
-    __device__ __forceinline__ int col(int e, int i) const { return scols[e * n + i]; }
+    __device__ __forceinline__ int col(int e, int i) const { return scols[e * n + i]; }  // e < len(i)
     __device__ __forceinline__ int dslot(int i) const { return sdslot[i] == 255 ? -1 : sdslot[i]; }
 };
 
 // The whole warp copies the pattern into `dst` (ilu_pattern_smem bytes).
 __device__ __forceinline__ void ilu_pattern_stage(IluPattern& Pt, const IluSchedule& S, const int32_t* rp,
-                                                  int16_t* dst, int lane) {
+                                                  unsigned char* dst, int lane) {
     const int n = Pt.n, k = Pt.k;
-    int16_t* cols = dst;
-    int16_t* src = cols + (size_t)k * n;
-    uint8_t* len = reinterpret_cast<uint8_t*>(src + (size_t)k * n);
+    uint16_t* rps = reinterpret_cast<uint16_t*>(dst);
+    uint8_t* cols = dst + 2 * (size_t)n;
+    uint8_t* len = cols + (size_t)k * n;
     uint8_t* dsl = len + n;
     uint8_t* levL = dsl + n;
     uint8_t* rowsL = levL + n + 1;
     uint8_t* levU = rowsL + n;
     uint8_t* rowsU = levU + n + 1;
     for (int i = lane; i < k * n; i += 32) {
-        cols[i] = (int16_t)ldg(Pt.xcols + i);
-        src[i] = (int16_t)ldg(Pt.xsrc + i);
+        const int c = ldg(Pt.xcols + i);
+        cols[i] = (uint8_t)(c >= 0 ? c : 255);
     }
     for (int i = lane; i < n; i += 32) {
         const int r0 = ldg(rp + i);
+        rps[i] = (uint16_t)r0;
         len[i] = (uint8_t)min(k, ldg(rp + i + 1) - r0);
         const int d = S.diag_pos[i];
         dsl[i] = (uint8_t)(d >= 0 ? d - r0 : 255);
@@ -79,8 +79,8 @@ __device__ __forceinline__ void ilu_pattern_stage(IluPattern& Pt, const IluSched
     for (int l = lane; l <= S.nlevL; l += 32) levL[l] = (uint8_t)S.levL_ptr[l];
     for (int l = lane; l <= S.nlevU; l += 32) levU[l] = (uint8_t)S.levU_ptr[l];
     __syncwarp();
+    Pt.srp = rps;
     Pt.scols = cols;
-    Pt.ssrc = src;
     Pt.slen = len;
     Pt.sdslot = dsl;
     Pt.slevL = levL;
@@ -100,10 +100,10 @@ __device__ __forceinline__ void spmv_gather(const IluPattern& Pt, const double* 
         const int row = tm.row(q);
         double sum = 0.0;
         if (row < Pt.n) {
+            const double* vr = vals + Pt.srp[row];  // slot j of the row is CSR entry srp[row] + j
             for (int j = 0; j < Pt.k; ++j) {
-                const int i = j * Pt.n + row;
-                const int col = Pt.scols[i];
-                if (col >= 0) sum = fma(ldg(vals + Pt.ssrc[i]), xs[col], sum);
+                const int col = Pt.scols[j * Pt.n + row];
+                if (col != 255) sum = fma(ldg(vr + j), xs[col], sum);
             }
         }
         y[q] = sum;
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(32, packed_cg_min_blocks(R))
     Pt.n = P.n;
     Pt.k = P.xk;
     ilu_pattern_stage(Pt, ilu_schedule(sched, P.n), P.row_ptrs,
-                      reinterpret_cast<int16_t*>(raw + (size_t)S * P.slice), lane);
+                      raw + (size_t)S * P.slice, lane);
     const double* vals = P.values + (size_t)sys * P.vps;
     for (size_t i = tm.tid; i < cells; i += L) {
         const int src = ldg(P.xsrc + i);
