@@ -241,15 +241,16 @@ class Uniform:
 
     def e2e(self, reps):
         bbs, torch = self.bbs, self.torch
-        hA = bbs.DeviceBatch.from_batch(self.A, "cpu", pin=True)
-        hb = torch.as_tensor(self.wl.b).pin_memory()
-        hx0 = torch.as_tensor(self.wl.x0)
-        # x is in/out: every call gets its own pinned copy of x0, made before
-        # the timed region (restoring one buffer on the host would time a
-        # host memcpy of the whole x that is not part of the call)
-        hxs = [hx0.clone().pin_memory() for _ in range(reps + 1)]
+        with host_memory_near(torch, self.dev) as near:
+            hA = bbs.DeviceBatch.from_batch(self.A, "cpu", pin=True)
+            hb = torch.as_tensor(self.wl.b).pin_memory()
+            hx0 = torch.as_tensor(self.wl.x0)
+            # x is in/out: every call gets its own pinned copy of x0, made
+            # before the timed region (restoring one buffer on the host would
+            # time a host memcpy of the whole x that is not part of the call)
+            hxs = [hx0.clone().pin_memory() for _ in range(reps + 1)]
+            hlog = bbs.Log.empty(self.num_batch, device="cpu", pin=True, inner=self.mixed)
         hx = hxs[0]
-        hlog = bbs.Log.empty(self.num_batch, device="cpu", pin=True, inner=self.mixed)
         self.h.solve_host(hA, hb, hxs[reps], self.opts, hlog)
         t0 = time.perf_counter()
         for i in range(reps):
@@ -259,7 +260,8 @@ class Uniform:
                + (hA.col_idxs.numel() * 4 if hA.col_idxs is not None else 0) + 2 * hb.numel() * 8)
         d2h = hx.numel() * 8 + self.num_batch * (4 + 8 + 4 + (4 if self.mixed else 0))
         return {"value": self.num_batch / dt, "unit": "systems/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "path": "bbs_solve_host (host buffers)"}
+                "d2h_bytes_per_step": d2h, "path": "bbs_solve_host (host buffers)",
+                "host_numa_node": near.node}
 
     def cpu(self, threads, budget_s):
         import oracle
@@ -385,6 +387,44 @@ def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0, s
     if (solver, precond) != ("bicgstab", "jacobi"):
         label = f"{label}_{solver}+{precond}"
     return Uniform(bbs, torch, dev, wl, fmt, opts, label)
+
+
+def gpu_numa_cpus(torch, dev):
+    """(NUMA node, its CPUs) of the GPU's host memory, from sysfs; (None,
+    None) when the machine does not say."""
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        bdf = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bdf}/numa_node") as f:
+            node = int(f.read())
+        if node < 0:
+            return None, None
+        cpus = set()
+        with open(f"/sys/devices/system/node/node{node}/cpulist") as f:
+            for part in f.read().strip().split(","):
+                a, _, b = part.partition("-")
+                cpus.update(range(int(a), int(b or a) + 1))
+        return node, (cpus & os.sched_getaffinity(0)) or None
+    except (OSError, ValueError, AttributeError, RuntimeError):
+        return None, None
+
+
+class host_memory_near:
+    """Run the block on the CPUs of the GPU's NUMA node (when known), so that
+    pinned buffers made there are first touched in memory next to the GPU."""
+
+    def __init__(self, torch, dev):
+        self.node, self.cpus = gpu_numa_cpus(torch, dev)
+
+    def __enter__(self):
+        self.saved = os.sched_getaffinity(0)
+        if self.cpus:
+            os.sched_setaffinity(0, self.cpus)
+        return self
+
+    def __exit__(self, *exc):
+        os.sched_setaffinity(0, self.saved)
+        return False
 
 
 def timed_solve(bbs, torch, h, dA, b, opts, reps=3):
