@@ -652,11 +652,19 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
         return s;
     cudaStream_t streams[2] = {h->stream, h->stream2};
     cudaError_t e = cudaSuccess;
+    // an error after the first copy waits for the work already queued, so
+    // that no copy still reads or writes the caller's buffers on return
+    const auto drain = [h]() {
+        for (cudaStream_t st : {h->copy_in, h->stream, h->stream2}) cudaStreamSynchronize(st);
+    };
 #define BBS_CP(dst, src, bytes, kind, st)                                          \
     if ((bytes) > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, kind, st)
     BBS_CP(d_rp, Ah->row_ptrs, rp_bytes, cudaMemcpyHostToDevice, h->copy_in);
     BBS_CP(d_ci, Ah->col_idxs, ci_bytes, cudaMemcpyHostToDevice, h->copy_in);
-    if (e != cudaSuccess) return cuda_fail(e, "pattern copy");
+    if (e != cudaSuccess) {
+        drain();
+        return cuda_fail(e, "pattern copy");
+    }
     for (size_t c = 0; c < nchunks; ++c) {
         cudaStream_t st = streams[c & 1];
         const size_t c0 = first[c], cb = count[c];
@@ -673,20 +681,29 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
         BBS_CP(xd, x_host + c0 * n, cb * n * 8, cudaMemcpyHostToDevice, h->copy_in);
         if (e == cudaSuccess) e = cudaEventRecord(h->chunk_in[c], h->copy_in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->chunk_in[c], 0);
-        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+        if (e != cudaSuccess) {
+            drain();
+            return cuda_fail(e, "host-to-device copy");
+        }
         bbs_batch_matrix Ac = Ad;
         Ac.num_batch = (int32_t)cb;
         Ac.values = reinterpret_cast<const double*>(v);
         Ac.values_f32 = reinterpret_cast<const float*>(v32);
         bbs_log dlog{static_cast<int32_t*>(d_it) + c0, static_cast<double*>(d_rr) + c0,
                      static_cast<int32_t*>(d_st) + c0, d_in ? static_cast<int32_t*>(d_in) + c0 : nullptr};
-        if ((s = bbs_solve(h, &Ac, bd, xd, o, &dlog, (c & 1) ? d_ws1 : d_ws0, ws_bytes, st)) != BBS_OK) return s;
+        if ((s = bbs_solve(h, &Ac, bd, xd, o, &dlog, (c & 1) ? d_ws1 : d_ws0, ws_bytes, st)) != BBS_OK) {
+            drain();
+            return s;
+        }
         BBS_CP(x_host + c0 * n, xd, cb * n * 8, cudaMemcpyDeviceToHost, st);
         BBS_CP(log_host->iters + c0, dlog.iters, cb * 4, cudaMemcpyDeviceToHost, st);
         BBS_CP(log_host->rel_res + c0, dlog.rel_res, cb * 8, cudaMemcpyDeviceToHost, st);
         BBS_CP(log_host->status + c0, dlog.status, cb * 4, cudaMemcpyDeviceToHost, st);
         if (log_host->inner_iters) BBS_CP(log_host->inner_iters + c0, dlog.inner_iters, cb * 4, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+        if (e != cudaSuccess) {
+            drain();
+            return cuda_fail(e, "device-to-host copy");
+        }
     }
 #undef BBS_CP
     for (cudaStream_t st : {h->copy_in, h->stream, h->stream2})
