@@ -221,6 +221,16 @@ bbs_status bbs_solve_host(bbs_handle *handle, const bbs_batch_matrix *A_host,
                           const double *b_host, double *x_host, const bbs_options *opts,
                           const bbs_log *log_host);
 
+/* The chunks bbs_solve_host cuts a batch into (host only, no GPU): for
+ * num_batch systems of input_bytes_per_system bytes of input each (values,
+ * b and x0), writes chunk c as systems [first[c], first[c] + count[c]) for
+ * up to max_chunks chunks, in order and covering the batch once, and
+ * returns the number of chunks: 0 for an empty batch, -1 when an argument
+ * is negative or NULL or more than max_chunks chunks would be needed (16
+ * always suffice). */
+int32_t bbs_host_chunk_plan(int64_t num_batch, int64_t input_bytes_per_system, int64_t *first,
+                            int64_t *count, int32_t max_chunks);
+
 /* bbs_solve without any caller workspace and without allocating: for callers
  * that cannot call cudaMalloc, such as code recording its work into a CUDA
  * graph under stream capture (allocation cannot be captured), latency-critical

@@ -139,6 +139,8 @@ def lib():
         L.bbs_paper_block_size.restype = C.c_int32
         L.bbs_default_block_size.argtypes = [C.c_int32, C.c_int32]
         L.bbs_default_block_size.restype = C.c_int32
+        L.bbs_host_chunk_plan.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32]
+        L.bbs_host_chunk_plan.restype = C.c_int32
         L.bbs_last_error.restype = C.c_char_p
         L.bbs_version.restype = C.c_char_p
         for name in ("bbs_default_options", "bbs_create", "bbs_destroy", "bbs_workspace_size", "bbs_describe", "bbs_check_pattern",
@@ -192,6 +194,15 @@ def bbs_paper_block_size(n: int, max_threads: int = 1024) -> int:
 
 def bbs_default_block_size(n: int, rows_per_thread: int = 5) -> int:
     return int(lib().bbs_default_block_size(n, rows_per_thread))
+
+
+def bbs_host_chunk_plan(num_batch: int, input_bytes_per_system: int, max_chunks: int = 16):
+    """bbs_host_chunk_plan: the (first, count) chunks bbs_solve_host cuts a
+    batch into, or None when it returns -1."""
+    first = (C.c_int64 * max(max_chunks, 1))()
+    count = (C.c_int64 * max(max_chunks, 1))()
+    n = int(lib().bbs_host_chunk_plan(num_batch, input_bytes_per_system, first, count, max_chunks))
+    return None if n < 0 else [(int(first[i]), int(count[i])) for i in range(n)]
 
 
 def bbs_version() -> str:

@@ -603,6 +603,26 @@ constexpr size_t kHostChunkBytes = 128u << 20;
 constexpr size_t kHostMinChunk = 2048;
 constexpr size_t kHostChunks = 8;
 
+int32_t bbs_host_chunk_plan(int64_t num_batch, int64_t input_bytes_per_system, int64_t* first, int64_t* count,
+                            int32_t max_chunks) {
+    if (num_batch < 0 || input_bytes_per_system < 0 || first == nullptr || count == nullptr || max_chunks < 0)
+        return -1;
+    const size_t B = (size_t)num_batch;
+    if (B == 0) return 0;
+    const size_t in_bytes = B * (size_t)input_bytes_per_system;
+    const size_t want = std::min(kHostChunks, std::max<size_t>(1, (in_bytes + kHostChunkBytes - 1) / kHostChunkBytes));
+    const size_t chunk = std::min(B, std::max(kHostMinChunk, (B + want - 1) / want));
+    // at most 2 + kHostChunks chunks: the ramp, then chunks of `chunk`
+    int32_t nc = 0;
+    for (size_t c0 = 0; c0 < B; c0 += (size_t)count[nc++]) {
+        if (nc == max_chunks) return -1;
+        const size_t ramp = nc == 0 ? chunk / 4 : nc == 1 ? chunk / 2 : chunk;
+        first[nc] = (int64_t)c0;
+        count[nc] = (int64_t)std::min(B - c0, std::max(kHostMinChunk, ramp));
+    }
+    return nc;
+}
+
 bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const double* b_host,
                           double* x_host, const bbs_options* o, const bbs_log* log_host) {
     if (h == nullptr) return fail(BBS_ERR_INVALID_ARG, "null handle");
@@ -628,17 +648,13 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
         (s = ensure(h, 8, B * 4, &d_st)) ||
         (s = ensure(h, 9, log_host->inner_iters ? B * 4 : 0, &d_in)))
         return s;
-    const size_t in_bytes = B * (vps * (Ah->values_f32 ? 12 : 8) + 2 * n * 8);
-    const size_t want = std::min(kHostChunks, std::max<size_t>(1, (in_bytes + kHostChunkBytes - 1) / kHostChunkBytes));
-    const size_t chunk = std::min(B, std::max(kHostMinChunk, (B + want - 1) / want));
-    // at most 2 + kHostChunks chunks: the ramp, then chunks of `chunk`
-    size_t first[16], count[16], nchunks = 0;
-    for (size_t c0 = 0; c0 < B; c0 += count[nchunks++]) {
-        if (nchunks == 16) return fail(BBS_ERR_UNSUPPORTED, "host batch cut into too many chunks");
-        const size_t ramp = nchunks == 0 ? chunk / 4 : nchunks == 1 ? chunk / 2 : chunk;
-        first[nchunks] = c0;
-        count[nchunks] = std::min(B - c0, std::max(kHostMinChunk, ramp));
-    }
+    int64_t first[16], count[16];
+    const int32_t planned = bbs_host_chunk_plan((int64_t)B, (int64_t)(vps * (Ah->values_f32 ? 12 : 8) + 2 * n * 8),
+                                                first, count, 16);
+    if (planned < 1) return fail(BBS_ERR_UNSUPPORTED, "host batch cut into too many chunks");
+    const size_t nchunks = (size_t)planned;
+    size_t chunk = 0;  // the largest chunk sizes the workspaces
+    for (size_t c = 0; c < nchunks; ++c) chunk = std::max(chunk, (size_t)count[c]);
     bbs_batch_matrix Ad = *Ah;
     Ad.row_ptrs = static_cast<const int32_t*>(d_rp);
     Ad.col_idxs = static_cast<const int32_t*>(d_ci);
@@ -667,7 +683,7 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
     }
     for (size_t c = 0; c < nchunks; ++c) {
         cudaStream_t st = streams[c & 1];
-        const size_t c0 = first[c], cb = count[c];
+        const size_t c0 = (size_t)first[c], cb = (size_t)count[c];
         char* v = static_cast<char*>(d_v) + c0 * vps * 8;
         char* v32 = Ah->values_f32 ? static_cast<char*>(d_v32) + c0 * vps * 4 : nullptr;
         double* bd = static_cast<double*>(d_b) + c0 * n;

@@ -80,3 +80,30 @@ def test_struct_layouts_match_header():
     assert C.sizeof(bbs.bbs_batch_matrix) == 24 + 4 * 8
     assert C.sizeof(bbs.bbs_log) == 32
     assert C.sizeof(bbs.bbs_launch_info) == 40 and bbs.bbs_launch_info.smem_bytes.offset == 24
+
+
+def test_host_chunk_plan():
+    """bbs_solve_host's chunks: in order, the batch covered once, at least
+    2,048 systems each but the last, led by a quarter and a half chunk, about
+    128 MB of input per full chunk and never more than 8 of them."""
+    from paper_2308_08417_gb300 import bbs
+
+    for B in (1, 7, 2047, 2048, 4096, 20001, 65536, 100001, 1 << 20):
+        for per in (0, 8, 8848, 90112, 1 << 20):
+            plan = bbs.bbs_host_chunk_plan(B, per)
+            assert plan and plan[0][0] == 0
+            assert all(a + n == b for (a, n), (b, _) in zip(plan, plan[1:]))
+            assert plan[-1][0] + plan[-1][1] == B
+            assert all(n >= min(2048, B) for _, n in plan[:-1]) and plan[-1][1] >= 1
+            full = max(n for _, n in plan)
+            assert sum(1 for _, n in plan if n == full) <= 8 and len(plan) <= 10
+            if len(plan) >= 4:  # plan[2] is a full chunk: the ramp leads it
+                c = plan[2][1]
+                assert plan[0][1] == max(2048, c // 4) and plan[1][1] == max(2048, c // 2)
+    # the headline batch: 65,536 systems of 672 values, b and x0 (7,680 bytes,
+    # 503 MB) in chunks of 4,096, 8,192, then 16,384 systems
+    assert [n for _, n in bbs.bbs_host_chunk_plan(65536, 672 * 8 + 2 * 144 * 8)] == [4096, 8192, 16384, 16384,
+                                                                                     16384, 4096]
+    assert bbs.bbs_host_chunk_plan(0, 100) == []
+    assert bbs.bbs_host_chunk_plan(-1, 100) is None
+    assert bbs.bbs_host_chunk_plan(65536, 8848, max_chunks=3) is None
