@@ -13,12 +13,19 @@ with autotuned team sizes). The default line carries short measurements of
 these under "extras".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload scale|mixed|uneven] [--systems N] [--no-extras]
+                  [--workload scale|mixed|uneven|learned|pele|sweep|peaks]
+                  [--systems N] [--shard] [--no-extras]
 
 --impl reference times the CPU oracle (plain C, OpenMP) on a bounded sample
 of the same workload, on the host cores.
 Multi-GPU: one process per GPU (torchrun), each solving its own full batch
-(weak scaling, no data-path collective); rank 0 prints the line.
+(weak scaling, no data-path collective); rank 0 prints the line. With
+--shard the ranks split one batch instead (strong scaling): rank r solves a
+contiguous range of systems (balanced by estimated cost for the uneven
+batch), and rank 0 gathers the iteration counts and statuses on the host.
+
+The default line ends with "speedups": the mixed-precision and learned-guess
+forms against plain FP64 on the same GPU (the metric's second half).
 """
 
 from __future__ import annotations
@@ -55,14 +62,8 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 # scales them to its own launch of the same shape by systems (traffic is the
 # compulsory bytes, which grow in proportion). A kernel run on a workload
 # without a capture reports null, and an entry is removed when its kernel
-# changes.
-#   bicgstab_packed_kernel:     profiles/bicgstab_packed_kernel_stencil2d5_n144.md
-#   bicgstab_folded_kernel:     profiles/bicgstab_folded_kernel_stencil2d5_n144.md
-#   cg_packed_kernel:           profiles/packed_cg_gmres_ilu_stencil2d5_n144.md
-#   refine_kernel:              profiles/refine_kernel_stencil2d9_n1024.md
-#   varsize_kernel:             profiles/varsize_kernel_uneven_n16-1024.md (first
-#                               20,000 systems of the uneven batch; per-system
-#                               bytes vary with n, so the scaling is approximate)
+# changes. The uneven batch's entry is the capture of its first 20,000
+# systems; per-system bytes vary with n, so its scaling is approximate.
 TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (134.9e6, 16384),
            ("bicgstab_folded_kernel", "stencil2d5_12x12"): (280.8e6, 32768),
            ("cg_packed_kernel", "sym_stencil2d5_12x12_cg+jacobi"): (133.05e6, 16384),
@@ -99,7 +100,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="scale",
-                   choices=["scale", "mixed", "uneven", "learned", "pele", "sweep"])
+                   choices=["scale", "mixed", "uneven", "learned", "pele", "sweep", "peaks"])
     p.add_argument("--format", default="csr", choices=["csr", "ell", "dense"],
                    help="batch format of the scale workload")
     p.add_argument("--solver", default="bicgstab", choices=["bicgstab", "cg", "gmres"],
@@ -110,6 +111,8 @@ def parse():
                    help="launch shape of the scale and mixed workloads (0: the library's choice)")
     p.add_argument("--systems", type=int, default=0,
                    help="solve only the first N systems of the workload (profiling runs)")
+    p.add_argument("--shard", action="store_true",
+                   help="ranks split one batch (strong scaling) instead of each solving a full batch")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-extras", action="store_true")
@@ -168,6 +171,32 @@ def subset_workload(wl, k):
     if not k:
         return wl
     return W.Workload(f"{wl.name}[:{k}]", wl.pattern, wl.csr_values[:k], wl.b[:k], wl.x0[:k])
+
+
+def span_workload(wl, span):
+    """Systems [begin, end) of a workload, under the whole workload's name (a
+    rank's share of a sharded batch)."""
+    if span is None:
+        return wl
+    b0, b1 = span
+    return W.Workload(wl.name, wl.pattern, wl.csr_values[b0:b1], wl.b[b0:b1], wl.x0[b0:b1])
+
+
+def uneven_cost(vb):
+    """Per-system cost estimate of an uneven batch, (2 nnz + 14 n) sqrt(n):
+    the work of one iteration times an iteration count growing like sqrt(n)."""
+    n = vb.sys_n().astype(np.float64)
+    return (2 * vb.sys_nnz() + 14 * n) * np.sqrt(n)
+
+
+def shard_span(workload, systems, rank, world):
+    """This rank's [begin, end) of the batch the workload names."""
+    from paper_2308_08417_gb300.sharding import cost_shard_range, shard_range
+
+    if workload == "uneven":
+        return cost_shard_range(uneven_cost(W.uneven(systems or 100000)), rank, world)
+    total = {"mixed": 16384, "scale": 65536}[workload]
+    return shard_range(min(systems, total) if systems else total, rank, world)
 
 
 class Uniform:
@@ -367,9 +396,9 @@ class Uneven:
 
 
 def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0, solver="bicgstab",
-                precond="jacobi"):
+                precond="jacobi", span=None):
     if name == "mixed":
-        wl = subset_workload(W.mixed_precision(), systems)
+        wl = span_workload(subset_workload(W.mixed_precision(), systems), span)
         # inner tolerance 1e-2: the fastest of 0.3 / 0.1 / 0.03 / 1e-2 / 1e-3 / 1e-4 in a sweep
         kw = dict(MIXED_OPTS)
         if tps:
@@ -379,8 +408,12 @@ def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0, s
         wl = subset_workload(W.mixed_precision(), systems)
         return Uniform(bbs, torch, dev, wl, "ell", dict(max_iters=2000), wl.name)
     if name == "uneven":
-        return Uneven(bbs, torch, dev, W.uneven(systems or 100000), tune=tune)
-    wl = subset_workload(W.plain_at_scale(symmetric=(solver == "cg")), systems)
+        vb = W.uneven(systems or 100000)
+        if span is not None:
+            vb = vb.slice(*span)
+            vb.name = vb.name.split("[")[0]
+        return Uneven(bbs, torch, dev, vb, tune=tune)
+    wl = span_workload(subset_workload(W.plain_at_scale(symmetric=(solver == "cg")), systems), span)
     opts = {"threads_per_system": tps} if tps else {}
     opts.update(solver=solver, precond=precond)
     label = wl.name if fmt == "csr" else f"{wl.name}_{fmt}"
@@ -560,19 +593,36 @@ def time_steps(r, torch, stream, steps, warmup, dist=None, sample_clocks=False, 
     return total_ms, solve_ms, (clk.summary() if clk else None)
 
 
-def roofline(r, solve_ms, mhz):
+def measured_peaks(bbs, h):
+    """FP64 and FP32 FMA rates of this GPU in TFLOP/s (bbs_fma_rate: 8 FMA
+    chains per thread, 8 blocks of 256 threads per SM, CUDA events)."""
+    try:
+        return {"fp64": bbs.bbs_fma_rate(h, "fp64") / 1e12, "fp32": bbs.bbs_fma_rate(h, "fp32") / 1e12,
+                "source": "bbs_fma_rate in this run (8 independent FMA chains per thread, "
+                          "8 x 256 threads per SM, one ~20 ms launch timed with CUDA events)"}
+    except Exception as e:  # report, do not hide
+        return {"error": repr(e)}
+
+
+def roofline(r, solve_ms, mhz, peaks=None):
     flops, arith = r.work()
     avg_s = statistics.mean(solve_ms) / 1e3
     per_clk = FP64_FLOP_PER_CLK_SM if arith == "fp64" else FP32_FLOP_PER_CLK_SM
     peak = per_clk * NUM_SMS * mhz * 1e6 / 1e12
     achieved = flops / avg_s / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic_bytes(r.kernel, r.label, r.num_batch), "kernel": r.kernel,
-            "arith": arith,
-            "peak_source": f"{arith.upper()} {per_clk:g} FLOP/clk/SM x {NUM_SMS} SMs x median SM clock {mhz:.0f} MHz"}
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "traffic": traffic_bytes(r.kernel, r.label, r.num_batch), "kernel": r.kernel,
+           "arith": arith,
+           "peak_source": f"nominal: {arith.upper()} {per_clk:g} FLOP/clk/SM x {NUM_SMS} SMs x median SM clock "
+                          f"{mhz:.0f} MHz"}
+    if peaks and arith in peaks:
+        out["measured_peak"] = peaks[arith]
+        out["frac_measured_peak"] = achieved / peaks[arith]
+        out["measured_peak_source"] = peaks["source"]
+    return out
 
 
-def extras(bbs, torch, dev, stream, mhz):
+def extras(bbs, torch, dev, stream, mhz, peaks=None):
     """Short measurements of the other forms on the same GPU."""
     out = {}
     try:
@@ -588,7 +638,7 @@ def extras(bbs, torch, dev, stream, mhz):
         out["mixed"] = {"workload": mix.label, "value": vm, "fp64_value": v64, "unit": "systems/s",
                         "speedup_vs_fp64": vm / v64, "max_rel_diff_vs_fp64": err,
                         "iterations": mix.summary(), "fp64_iterations": f64.summary(),
-                        "roofline": roofline(mix, ms, mhz), "fp64_roofline": roofline(f64, ms64, mhz)}
+                        "roofline": roofline(mix, ms, mhz, peaks), "fp64_roofline": roofline(f64, ms64, mhz, peaks)}
         del f64, mix
         torch.cuda.empty_cache()
         # the same solve with the caller's FP32 copy of the values: the
@@ -610,7 +660,7 @@ def extras(bbs, torch, dev, stream, mhz):
         tot, ms, _ = time_steps(ow, torch, stream, 5, 2)
         out["one_system_per_warp"] = {"workload": ow.wl.name, "value": ow.num_batch * 5 / (tot / 1e3),
                                       "unit": "systems/s", "launch": ow.launch, "iterations": ow.summary(),
-                                      "roofline": roofline(ow, ms, mhz)}
+                                      "roofline": roofline(ow, ms, mhz, peaks)}
         del ow
     except Exception as e:
         out["one_system_per_warp"] = {"error": repr(e)}
@@ -620,7 +670,7 @@ def extras(bbs, torch, dev, stream, mhz):
             kr = Uniform(bbs, torch, dev, wl, "csr", dict(solver=solver), f"{wl.name}_{solver}+jacobi")
             tot, ms, _ = time_steps(kr, torch, stream, 5, 2)
             out[solver] = {"workload": kr.label, "value": kr.num_batch * 5 / (tot / 1e3), "unit": "systems/s",
-                           "launch": kr.launch, "iterations": kr.summary(), "roofline": roofline(kr, ms, mhz)}
+                           "launch": kr.launch, "iterations": kr.summary(), "roofline": roofline(kr, ms, mhz, peaks)}
             del kr
         except Exception as e:
             out[solver] = {"error": repr(e)}
@@ -630,13 +680,13 @@ def extras(bbs, torch, dev, stream, mhz):
         tot, ms, _ = time_steps(il, torch, stream, 5, 2)
         out["ilu0"] = {"workload": il.label, "value": il.num_batch * 5 / (tot / 1e3),
                        "unit": "systems/s", "iterations": il.summary(), "launch": il.launch,
-                       "roofline": roofline(il, ms, mhz),
+                       "roofline": roofline(il, ms, mhz, peaks),
                        "note": "BiCGSTAB + ILU(0) (level-scheduled factorisation and triangular solves)"}
         del il
     except Exception as e:
         out["ilu0"] = {"error": repr(e)}
     try:
-        out["learned"] = learned_run(bbs, torch, dev, eval_steps=32)
+        out["learned"] = learned_run(bbs, torch, dev, eval_steps=192)
     except Exception as e:
         out["learned"] = {"error": repr(e)}
     try:
@@ -644,7 +694,7 @@ def extras(bbs, torch, dev, stream, mhz):
         tot, ms, _ = time_steps(un, torch, stream, 5, 2)
         out["uneven"] = {"workload": un.label, "value": un.num_batch * 5 / (tot / 1e3),
                          "unit": "systems/s", "iterations": un.summary(),
-                         "roofline": roofline(un, ms, mhz), "launches_per_step": "1 graph (memset + kernel)"}
+                         "roofline": roofline(un, ms, mhz, peaks), "launches_per_step": "1 graph (memset + kernel)"}
         del un
     except Exception as e:
         out["uneven"] = {"error": repr(e)}
@@ -723,6 +773,15 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
+    if args.workload == "peaks":
+        h = bbs.Handle(local)
+        with ClockSampler(local) as clk:
+            pk = measured_peaks(bbs, h)
+        if rank == 0:
+            print(json.dumps({"workload": "peaks", "unit": "TFLOP/s", **pk, "clocks": clk.summary(),
+                              "nominal_fp64": FP64_FLOP_PER_CLK_SM * NUM_SMS * 2.07e9 / 1e12,
+                              "nominal_fp32": FP32_FLOP_PER_CLK_SM * NUM_SMS * 2.07e9 / 1e12}), flush=True)
+        return
     if args.workload in ("pele", "sweep"):
         res = pele_runs(bbs, torch, dev) if args.workload == "pele" else sweep_runs(bbs, torch, dev)
         if rank == 0:
@@ -741,34 +800,49 @@ def main():
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
+    span = shard_span(args.workload, args.systems, rank, world) if args.shard else None
     r = make_runner(args.workload, bbs, torch, dev, args.systems, tune=not args.no_tune, fmt=args.format,
-                    tps=args.threads_per_system, solver=args.solver, precond=args.precond)
+                    tps=args.threads_per_system, solver=args.solver, precond=args.precond, span=span)
     total_ms, solve_ms, clocks = time_steps(r, torch, stream, args.steps, args.warmup, dist,
                                             sample_clocks=True, dev_index=local)
     total_ms = max_over_ranks(total_ms, dist, dev)  # the job's time is its slowest rank's
     mhz = clocks.get("sm_mhz") or 2070.0
-    value = r.num_batch * world * args.steps / (total_ms / 1e3)
+    if args.shard:  # one batch split over the ranks
+        job_systems = int(r.num_batch)
+        if dist is not None:
+            t = torch.tensor([job_systems], dtype=torch.int64, device=dev)
+            dist.all_reduce(t)
+            job_systems = int(t.item())
+    else:  # every rank solves its own full batch
+        job_systems = r.num_batch * world
+    value = job_systems * args.steps / (total_ms / 1e3)
     avg_solve_s = statistics.mean(solve_ms) / 1e3
     hbm_bytes = r.compulsory_bytes()
+    peaks = measured_peaks(bbs, r.h)
     line = {"metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
             "dtype": "f64+f32" if r.mixed else "f64", "data": "synthetic",
             "config": {"workload": r.label, "num_batch_per_gpu": r.num_batch, "tol": 1e-10,
                        "solver": f"{args.solver}+{args.precond}" if args.workload == "scale" else "bicgstab+jacobi",
                        "l2": "inputs larger than L2 (no flush)"},
             "gpu_launches": args.steps * r.launches_per_step,
             "launch": getattr(r, "launch", None),
-            "clocks": clocks, "roofline": roofline(r, solve_ms, mhz),
+            "clocks": clocks, "roofline": roofline(r, solve_ms, mhz, peaks),
             "iterations": r.summary(),
             "compulsory_hbm": {"bytes": hbm_bytes, "GB/s": hbm_bytes / avg_solve_s / 1e9,
                                "frac_of_hbm": hbm_bytes / avg_solve_s / 1e9 / HBM_GBS}}
+    if args.shard:
+        line["config"]["shard"] = {"span": list(span), "job_systems": job_systems,
+                                   "split": "cost-balanced contiguous ranges" if args.workload == "uneven"
+                                   else "contiguous ranges"}
+        line["gathered"] = gather_logs(r, torch, dist, dev)
     if hasattr(r, "streamed_bytes"):
         sb = r.streamed_bytes()
         line["streamed_matrix_hbm"] = {"bytes": sb, "GB/s": sb / avg_solve_s / 1e9,
                                        "frac_of_hbm": sb / avg_solve_s / 1e9 / HBM_GBS,
                                        "note": "values re-read by every SpMV, as an unstaged design would"}
-    if rank == 0 and not args.no_e2e:
+    if rank == 0 and not args.no_e2e and not args.shard:
         line["e2e"] = r.e2e(max(2, min(args.steps, 5)))
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
@@ -782,11 +856,49 @@ def main():
     if rank == 0 and world == 1 and args.workload == "scale" and not args.no_extras and not args.systems:
         del r
         torch.cuda.empty_cache()
-        line["extras"] = extras(bbs, torch, dev, stream, mhz)
+        ex = extras(bbs, torch, dev, stream, mhz, peaks)
+        line["extras"] = ex
+        line["speedups"] = speedups(ex, value)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def gather_logs(r, torch, dist, dev):
+    """Host-side collection of a sharded run's per-system outcome (after the
+    timed region): every rank's iteration counts and statuses, concatenated in
+    rank order on rank 0."""
+    its = r.log.iters.cpu().numpy()
+    st = r.log.status.cpu().numpy()
+    parts = [(its, st)]
+    if dist is not None:
+        parts = [None] * dist.get_world_size()
+        dist.all_gather_object(parts, (its, st))
+    it = np.concatenate([p[0] for p in parts])
+    sa = np.concatenate([p[1] for p in parts])
+    return {"systems": int(it.size), "converged": int((sa == 0).sum()), "iters_mean": float(it.mean()),
+            "collective": "host-side gather of the logs after the timed region"}
+
+
+def speedups(ex, plain_value):
+    """The metric's second half, compact: each form against plain FP64 BiCGSTAB
+    on the same GPU (ratios of systems/s at rel. residual 1e-10)."""
+    out = {"plain_fp64_systems_per_s": round(plain_value)}
+    m = ex.get("mixed", {})
+    if "speedup_vs_fp64" in m:
+        out["mixed_vs_fp64"] = round(m["speedup_vs_fp64"], 3)
+        out["mixed"] = {"systems_per_s": round(m["value"]), "fp64_systems_per_s": round(m["fp64_value"]),
+                        "workload": m["workload"], "max_rel_diff_vs_fp64": m["max_rel_diff_vs_fp64"]}
+    lr = ex.get("learned", {})
+    if "speedup" in lr:
+        out["learned_vs_prev_x"] = round(lr["speedup"], 3)
+        out["learned_vs_zero"] = round(lr["speedup_vs_zero_guess"], 3)
+        out["learned"] = {"workload": lr["workload"], "eval_steps": lr["eval_steps"],
+                          "iters": [round(lr["iters_learned"], 2), round(lr["iters_base"], 2),
+                                    round(lr["iters_zero_guess"], 2)],
+                          "iters_order": "learned, x(t-1), zero"}
+    return out
 
 
 if __name__ == "__main__":

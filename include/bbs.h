@@ -87,8 +87,15 @@ typedef struct {
     int32_t ell_k; /* ELL: width (max nonzeros per row). CSR: 0, or the
                       largest number of nonzeros in any row; with it, small
                       systems can run packed several to a warp (their values
-                      staged in ELL order). A CSR row longer than a given
-                      ell_k makes every system of that call report
+                      staged in ELL order). A packed CSR solve whose pattern
+                      has a row longer than ell_k returns
+                      BBS_ERR_INVALID_ARG before any launch. The first such
+                      solve with a given row_ptrs address (and n, nnz,
+                      ell_k) reads the row pointers back on its stream and
+                      waits for them; the handle remembers the answer for
+                      the next 16 patterns. A pattern rewritten in place
+                      under a remembered address is caught on the device
+                      instead: every system of the call reports
                       BBS_SYS_NAN. DENSE: ignored. */
     const int32_t *row_ptrs;
     const int32_t *col_idxs;
@@ -231,24 +238,26 @@ bbs_status bbs_solve_host(bbs_handle *handle, const bbs_batch_matrix *A_host,
 int32_t bbs_host_chunk_plan(int64_t num_batch, int64_t input_bytes_per_system, int64_t *first,
                             int64_t *count, int32_t max_chunks);
 
-/* bbs_solve without any caller workspace and without allocating: for callers
- * that cannot call cudaMalloc, such as code recording its work into a CUDA
- * graph under stream capture (allocation cannot be captured), latency-critical
- * loops that must not touch the allocator, and hosts that keep device memory
- * under their own pool or budget. The paper has no counterpart: it is an
- * interface addition of this library.
+/* bbs_solve without any caller workspace and without allocating, for callers
+ * that cannot call cudaMalloc: hosts whose device memory is already reserved
+ * by another allocator (a framework's caching pool, a server's arena, a fixed
+ * budget), and loops that must not wait on the allocator (cudaFree
+ * synchronises the device). The paper has no counterpart: it is an interface
+ * addition of this library.
  * Arguments and results are those of bbs_solve (all DEVICE pointers, x in/out,
- * asynchronous on `stream`). The scratch bbs_solve would take from the
- * workspace (the FP32 copy of the values in mixed mode, the GMRES basis when it
- * does not fit in shared memory) comes instead from one static 64 MiB device
- * array inside the library, which every GPU that loads the library keeps until
- * the process exits. A batch whose scratch exceeds 64 MiB is solved in
- * consecutive chunks of systems on `stream`; a single system needing more than
- * 64 MiB is rejected with BBS_ERR_UNSUPPORTED. The first call on a device looks
- * up the array's device address, so make that call before any stream capture.
- * Every call shares the one array: calls that overlap on the GPU (other
- * streams, other host threads) race on it and must be serialised by the
- * caller. Calls no cudaMalloc, cudaFree or allocating library routine. */
+ * asynchronous on `stream`); the results are bit for bit those of bbs_solve
+ * with a workspace. The scratch bbs_solve would take from the workspace (the
+ * FP32 copy of the values in mixed mode when they are not staged, the GMRES
+ * basis when it does not fit in shared memory) comes instead from one static
+ * 64 MiB device array inside the library, which every GPU that loads the
+ * library keeps until the process exits. A batch whose scratch exceeds 64 MiB
+ * is solved in consecutive chunks of systems on `stream`; a single system
+ * needing more than 64 MiB is rejected with BBS_ERR_UNSUPPORTED. The first
+ * call on a device looks up the array's device address, so make that call
+ * before any stream capture. Every call shares the one array, which keeps the
+ * last call's contents: calls that overlap on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller. Calls no
+ * cudaMalloc, cudaFree or allocating library routine. */
 bbs_status bbs_solve_noalloc(bbs_handle *handle, const bbs_batch_matrix *A, const double *b,
                              double *x, const bbs_options *opts, const bbs_log *log,
                              void *stream);
@@ -414,10 +423,24 @@ bbs_status bbs_gemm_bf16(bbs_handle *handle, int32_t kind, const uint16_t *A, in
 bbs_status bbs_mlp_get_grads(bbs_mlp *mlp, float *grads, void *stream);
 /* Network output (standardised change) for M feature rows: out [M, n] FP32. */
 bbs_status bbs_mlp_forward(bbs_mlp *mlp, const uint16_t *feats, int32_t M, float *out, void *stream);
-/* Initial guesses for a whole batch: x0 = x_prev + predicted change (DEVICE
- * FP64 [num_batch * n]). */
+/* Initial guesses for a whole batch: x0 = x_prev + gamma * predicted change
+ * (DEVICE FP64 [num_batch * n]); gamma is 1 until a gate is fitted. */
 bbs_status bbs_mlp_predict(bbs_mlp *mlp, const bbs_batch_matrix *A, const double *b,
                            const double *x_prev, double *x0, void *stream);
+/* The gate on the predicted change c, fitted on steps held out from training.
+ * An initial guess is there to speed the solve up (Sec. 2.1); with the gate
+ * the guess falls back to x_prev where the network carries no signal.
+ * gate_observe runs the network on one step (A, b, x_prev as for predict)
+ * and accumulates sum c.d and sum c.c over the batch in FP64, d = x_next -
+ * x_prev the true change (DEVICE, num_batch*n). gate_finalize sets gamma =
+ * sum c.d / sum c.c limited to [0, 1] (0 if sum c.c = 0), the least-squares
+ * scale: on the observed steps, sum ||d - gamma c||^2 <= sum ||d||^2, the
+ * error of x0 = x_prev; it clears the sums. Asynchronous on stream.
+ * get_gate copies gamma to the host (synchronous). */
+bbs_status bbs_mlp_gate_observe(bbs_mlp *mlp, const bbs_batch_matrix *A, const double *b,
+                                const double *x_prev, const double *x_next, void *stream);
+bbs_status bbs_mlp_gate_finalize(bbs_mlp *mlp, void *stream);
+bbs_status bbs_mlp_get_gate(bbs_mlp *mlp, double *gamma);
 
 /* Threads per system by the rule of Sec. 3.6: at least n, a multiple of the
  * warp size 32, at most `max_threads` (the device maximum, 1024 on GB300).
@@ -430,6 +453,16 @@ int32_t bbs_paper_block_size(int32_t n, int32_t max_threads);
  * solvers (fewest FP64 instructions per system) and 4 for the mixed mode.
  * Host only. */
 int32_t bbs_default_block_size(int32_t n, int32_t rows_per_thread);
+
+/* Measured arithmetic peak of the handle's device, the denominator of the
+ * FP64 solvers' roofline (the paper compares each GPU's FP64 peak, Table "GPUs
+ * specifications", and places its solver on a roofline, Sec. "Roofline
+ * analysis"). precision 0 measures FP64 FMAs, 1 FP32 FMAs: 8 blocks of 256
+ * threads per SM, 8 independent FMA chains per thread, timed with CUDA events
+ * over one launch of about 20 ms on a stream of its own. *flop_per_s receives
+ * the rate (an FMA counts 2 FLOP). Synchronous; allocates no device memory.
+ * BBS_ERR_INVALID_ARG for a NULL argument or another precision. */
+bbs_status bbs_fma_rate(bbs_handle *handle, int32_t precision, double *flop_per_s);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char *bbs_last_error(void);

@@ -132,6 +132,9 @@ def lib():
         L.bbs_mlp_train_step.argtypes = [vp, vp, vp, vp, i32, C.c_float, vp, st]
         L.bbs_mlp_forward.argtypes = [vp, vp, i32, vp, st]
         L.bbs_mlp_predict.argtypes = [vp, P(bbs_batch_matrix), vp, vp, vp, st]
+        L.bbs_mlp_gate_observe.argtypes = [vp, P(bbs_batch_matrix), vp, vp, vp, st]
+        L.bbs_mlp_gate_finalize.argtypes = [vp, st]
+        L.bbs_mlp_get_gate.argtypes = [vp, P(C.c_double)]
         L.bbs_mlp_set_gemm.argtypes = [vp, i32]
         L.bbs_mlp_check.argtypes = [vp]
         L.bbs_gemm_bf16.argtypes = [vp, i32, vp, i32, vp, i32, i32, i32, i32, vp, i32]
@@ -140,6 +143,7 @@ def lib():
         L.bbs_default_block_size.argtypes = [C.c_int32, C.c_int32]
         L.bbs_default_block_size.restype = C.c_int32
         L.bbs_host_chunk_plan.argtypes = [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32]
+        L.bbs_fma_rate.argtypes = [C.c_void_p, C.c_int32, P(C.c_double)]
         L.bbs_host_chunk_plan.restype = C.c_int32
         L.bbs_last_error.restype = C.c_char_p
         L.bbs_version.restype = C.c_char_p
@@ -150,7 +154,8 @@ def lib():
                      "bbs_mlp_set_params", "bbs_mlp_get_grads", "bbs_mlp_observe",
                      "bbs_mlp_finalize_stats", "bbs_mlp_make_samples", "bbs_mlp_gradients",
                      "bbs_mlp_train_step", "bbs_mlp_forward", "bbs_mlp_predict", "bbs_mlp_set_gemm",
-                     "bbs_mlp_check", "bbs_gemm_bf16"):
+                     "bbs_mlp_check", "bbs_gemm_bf16", "bbs_fma_rate", "bbs_mlp_gate_observe",
+                     "bbs_mlp_gate_finalize", "bbs_mlp_get_gate"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -203,6 +208,14 @@ def bbs_host_chunk_plan(num_batch: int, input_bytes_per_system: int, max_chunks:
     count = (C.c_int64 * max(max_chunks, 1))()
     n = int(lib().bbs_host_chunk_plan(num_batch, input_bytes_per_system, first, count, max_chunks))
     return None if n < 0 else [(int(first[i]), int(count[i])) for i in range(n)]
+
+
+def bbs_fma_rate(handle: "Handle", precision: str = "fp64") -> float:
+    """bbs_fma_rate: measured FMA throughput of the handle's device in FLOP/s
+    (precision "fp64" or "fp32")."""
+    out = C.c_double()
+    _check(lib().bbs_fma_rate(handle._h, {"fp64": 0, "fp32": 1}[precision], C.byref(out)), "bbs_fma_rate")
+    return float(out.value)
 
 
 def bbs_version() -> str:
@@ -546,6 +559,20 @@ class MLP:
         out = torch.empty(M, self.n, dtype=torch.float32, device=self.device)
         _check(lib().bbs_mlp_forward(self._p, _ptr(feats), M, _ptr(out), _stream(feats)), "bbs_mlp_forward")
         return out
+
+    def gate_observe(self, A: DeviceBatch, b, x_prev, x_next):
+        s = A.struct()
+        _check(lib().bbs_mlp_gate_observe(self._p, C.byref(s), _ptr(b), _ptr(x_prev), _ptr(x_next), _stream(b)),
+               "bbs_mlp_gate_observe")
+
+    def gate_finalize(self):
+        _check(lib().bbs_mlp_gate_finalize(self._p, C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)),
+               "bbs_mlp_gate_finalize")
+
+    def gate(self) -> float:
+        g = C.c_double()
+        _check(lib().bbs_mlp_get_gate(self._p, C.byref(g)), "bbs_mlp_get_gate")
+        return float(g.value)
 
     def predict(self, A: DeviceBatch, b, x_prev, x0=None):
         x0 = torch.empty_like(x_prev) if x0 is None else x0

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -31,6 +32,16 @@ struct bbs_handle {
     // device buffers owned for bbs_solve_host (grow only)
     void* buf[12] = {nullptr};
     size_t cap[12] = {0};
+    // CSR patterns whose row-length bound (ell_k) has been checked against
+    // their row pointers, most recent first (see csr_bound_ok)
+    struct CheckedPattern {
+        const int32_t* row_ptrs;
+        int32_t n, nnz, ell_k, longest;
+    };
+    static constexpr int kChecked = 16;
+    CheckedPattern checked[kChecked] = {};
+    int num_checked = 0;
+    std::mutex checked_mutex;
 };
 
 namespace {
@@ -245,8 +256,8 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
     const bool mixed = o->precision == BBS_PRECISION_MIXED_IR;
     const size_t vps = vals_per_system(A);
     size_t base;
-    if (mixed) {
-        base = 256 * 8 + (size_t)p->n_pad * 8 + 256 * 4 + 2 * (size_t)p->n_pad * 4;
+    if (mixed) {  // FP32 SpMV inputs keep a zero after their last entry
+        base = 256 * 8 + (size_t)p->n_pad * 8 + 256 * 4 + 2 * ((size_t)p->n_pad + 2) * 4;
     } else {
         base = 256 * 8 + 2 * (size_t)p->n_pad * 8;
         if (o->solver == BBS_SOLVER_GMRES) {
@@ -273,7 +284,12 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
         p->ws_ilu = align_up(bbs::ilu_workspace_bytes(n), 256);
         return BBS_OK;
     }
-    const size_t stage_bytes = align_up(vps * (mixed ? 4 : 8), 16);
+    // mixed mode on ELL stages (FP32 value, column) pairs for every row slot
+    // of the block, R * ell_k * threads of them (the refinement kernel's
+    // PairOp32); otherwise the values in their own layout
+    const size_t stage_bytes = (mixed && A->fmt == BBS_FMT_ELL)
+                                   ? align_up((size_t)p->R * (size_t)A->ell_k * (size_t)p->threads * 8, 16)
+                                   : align_up(vps * (mixed ? 4 : 8), 16);
     const size_t limit = (size_t)h->max_smem_optin;
     bool stage = false;
     if (o->values_in_smem == 1)
@@ -294,9 +310,14 @@ size_t workspace_bytes(const Plan& p) {
     return align_up(p.ws_gmres, 256) + p.ws_f32 + p.ws_ilu + p.ws_tables;
 }
 
-// BiCGSTAB with staged values and Jacobi runs the Jacobi-folded kernel.
-const void* pick_kernel(const bbs_options* o, int fmt, int R, bool staged) {
-    if (o->precision == BBS_PRECISION_MIXED_IR) return bbs::refine_fn(fmt, R);
+// BiCGSTAB with staged values and Jacobi runs the Jacobi-folded kernel; the
+// mixed mode on ELL with staged values takes an instance for its ELL width
+// when there is one.
+const void* pick_kernel(const bbs_options* o, int fmt, int R, bool staged, int ell_k) {
+    if (o->precision == BBS_PRECISION_MIXED_IR) {
+        const void* fn = (fmt == BBS_FMT_ELL && staged) ? bbs::refine_ell_fn(R, ell_k) : nullptr;
+        return fn != nullptr ? fn : bbs::refine_fn(fmt, R);
+    }
     switch (o->solver) {
         case BBS_SOLVER_CG: return bbs::cg_fn(fmt, R);
         case BBS_SOLVER_GMRES: return bbs::gmres_fn(fmt, R);
@@ -312,6 +333,56 @@ cudaError_t allow_smem(const void* fn, size_t smem) {
     if (smem <= 48 * 1024) return cudaSuccess;
     std::lock_guard<std::mutex> lock(g_attr_mutex);
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Packed CSR solves stage each system's values through an ELL table of
+// width ell_k, so a row longer than ell_k is an argument error. The row
+// pointers are device data: the first solve with a pattern (keyed by its
+// row_ptrs address, n, nnz and ell_k) copies them back on the solve's stream
+// and waits for them, and the handle remembers the result, so later solves
+// with the same pattern launch without waiting. (A pattern rewritten in place
+// behind a remembered key is still caught on the device, where every system
+// then reports BBS_SYS_NAN.)
+void remember_pattern(bbs_handle* h, const bbs_batch_matrix* A, int32_t longest) {
+    std::lock_guard<std::mutex> lock(h->checked_mutex);
+    int keep = h->num_checked < bbs_handle::kChecked ? h->num_checked : bbs_handle::kChecked - 1;
+    for (int i = 0; i < h->num_checked; ++i) {
+        const auto& c = h->checked[i];
+        if (c.row_ptrs == A->row_ptrs && c.n == A->n && c.nnz == A->nnz && c.ell_k == A->ell_k) {
+            keep = i;
+            break;
+        }
+    }
+    for (int i = keep; i > 0; --i) h->checked[i] = h->checked[i - 1];
+    h->checked[0] = {A->row_ptrs, A->n, A->nnz, A->ell_k, longest};
+    if (keep == h->num_checked) ++h->num_checked;
+}
+
+bbs_status csr_bound_ok(bbs_handle* h, const bbs_batch_matrix* A, cudaStream_t st) {
+    int32_t longest = -1;
+    {
+        std::lock_guard<std::mutex> lock(h->checked_mutex);
+        for (int i = 0; i < h->num_checked; ++i) {
+            const auto& c = h->checked[i];
+            if (c.row_ptrs == A->row_ptrs && c.n == A->n && c.nnz == A->nnz && c.ell_k == A->ell_k) {
+                longest = c.longest;
+                break;
+            }
+        }
+    }
+    if (longest < 0) {
+        std::vector<int32_t> rp((size_t)A->n + 1);
+        cudaError_t e = cudaMemcpyAsync(rp.data(), A->row_ptrs, rp.size() * sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the CSR row pointers back");
+        longest = 0;
+        for (int32_t i = 0; i < A->n; ++i) longest = std::max(longest, rp[(size_t)i + 1] - rp[i]);
+        remember_pattern(h, A, longest);
+    }
+    if (longest > A->ell_k)
+        return fail(BBS_ERR_INVALID_ARG, "a CSR row has %d nonzeros, more than ell_k = %d", longest, A->ell_k);
+    return BBS_OK;
 }
 
 }  // namespace
@@ -491,6 +562,7 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
     if (A->num_batch == 0) return BBS_OK;
     cudaSetDevice(h->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p.ws_tables > 0 && (s = csr_bound_ok(h, A, st)) != BBS_OK) return s;
 
     bbs::SolveParams P{};
     P.n = A->n;
@@ -567,7 +639,7 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
         e = cudaLaunchKernel(fn, dim3(blocks), dim3(32), args, p.smem, st);
         return e == cudaSuccess ? BBS_OK : cuda_fail(e, "packed solver launch");
     }
-    const void* fn = pick_kernel(o, A->fmt, p.R, p.stage);
+    const void* fn = pick_kernel(o, A->fmt, p.R, p.stage, A->ell_k);
     if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     void* args[] = {&P};
     e = cudaLaunchKernel(fn, dim3((unsigned)A->num_batch), dim3((unsigned)p.threads), args, p.smem, st);
@@ -661,6 +733,16 @@ bbs_status bbs_solve_host(bbs_handle* h, const bbs_batch_matrix* Ah, const doubl
     Ad.values = static_cast<const double*>(d_v);
     Ad.values_f32 = static_cast<const float*>(d_v32);
     Ad.num_batch = (int32_t)chunk;
+    if (Ah->fmt == BBS_FMT_CSR && Ah->ell_k > 0) {
+        // the row pointers are on the host here: check the row-length bound
+        // directly, and record the result for the device copy that bbs_solve
+        // will see (the handle's buffer may have held another pattern before)
+        int32_t longest = 0;
+        for (int32_t i = 0; i < Ah->n; ++i) longest = std::max(longest, Ah->row_ptrs[i + 1] - Ah->row_ptrs[i]);
+        if (longest > Ah->ell_k)
+            return fail(BBS_ERR_INVALID_ARG, "a CSR row has %d nonzeros, more than ell_k = %d", longest, Ah->ell_k);
+        remember_pattern(h, &Ad, longest);
+    }
     size_t ws_bytes = 0;  // the largest chunk's workspace; one per stream
     if ((s = bbs_workspace_size(h, &Ad, o, &ws_bytes)) != BBS_OK) return s;
     if ((s = ensure(h, 10, ws_bytes, &d_ws0)) != BBS_OK ||

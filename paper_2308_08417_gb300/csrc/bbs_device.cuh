@@ -197,8 +197,26 @@ __device__ __forceinline__ void spmv_staged(const Mat<V>& A, const V* __restrict
     }
 }
 
-// Copy `count` values from global to shared memory with the whole block
-// (16-byte vector loads when both ends allow it).
+// Asynchronous global -> shared copies (cp.async): the data never pass
+// through registers, so a thread's whole share of a staging loop is in
+// flight at once instead of one load latency per element. The copies land
+// after cp_async_wait_all() in the issuing thread and are visible to the
+// others after the team's next barrier. 16-byte copies bypass L1 (the
+// values are read once); 8-byte copies (gathers) go through it.
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(s));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(s));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy `count` values from global to shared memory with the whole team:
+// 16-byte asynchronous copies when the source is 16-byte aligned (the
+// destination always is), the ragged tail by plain loads. The caller
+// synchronises the team afterwards.
 template <typename V>
 __device__ __forceinline__ void stage_values(const V* __restrict__ g, V* __restrict__ s,
                                              size_t count, const Team& tm) {
@@ -209,10 +227,11 @@ __device__ __forceinline__ void stage_values(const V* __restrict__ g, V* __restr
         const size_t nv = count / kVec;
         const uint4* gv = reinterpret_cast<const uint4*>(g);
         uint4* sv = reinterpret_cast<uint4*>(s);
-        for (size_t j = tm.tid; j < nv; j += tm.nt) sv[j] = __ldg(gv + j);
+        for (size_t j = tm.tid; j < nv; j += tm.nt) cp_async16(sv + j, gv + j);
         i = nv * kVec;
     }
     for (size_t j = i + tm.tid; j < count; j += tm.nt) s[j] = ldg(g + j);
+    cp_async_wait_all();
 }
 
 // ------------------------------------------------------------ reductions
@@ -286,12 +305,37 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* red, int& parity, const
     if (tm.nwarps == 1) return;
     T* buf = red + parity * 128;
     parity ^= 1;
+    if constexpr (sizeof(T) == 4) {
+        if (tm.nwarps <= 32) {  // FP32: one 16-byte slot per warp, read back as 16-byte broadcasts
+            float4* b4 = reinterpret_cast<float4*>(buf);
+            if (tm.lane == 0)
+                b4[tm.warp] = make_float4(v[0], NV > 1 ? v[NV > 1 ? 1 : 0] : 0.0f, NV > 2 ? v[NV > 2 ? 2 : 0] : 0.0f,
+                                          NV > 3 ? v[NV > 3 ? 3 : 0] : 0.0f);
+            tm.sync();
+            float4 s = b4[0];
+            for (int w = 1; w < tm.nwarps; ++w) {
+                const float4 t = b4[w];
+                s.x += t.x;
+                s.y += t.y;
+                s.z += t.z;
+                s.w += t.w;
+            }
+            v[0] = s.x;
+            if constexpr (NV > 1) v[1] = s.y;
+            if constexpr (NV > 2) v[2] = s.z;
+            if constexpr (NV > 3) v[3] = s.w;
+            return;
+        }
+    }
     if (tm.lane == 0) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) buf[tm.warp * 4 + j] = v[j];
     }
     tm.sync();
-    if (tm.nwarps <= 4) {
+    // serial sums over the warps' partials: FP64 up to 4 warps (FP64 adds are
+    // scarce), FP32 up to 8 (a short dependent chain beats a second shuffle
+    // tree there)
+    if (tm.nwarps <= (sizeof(T) == 4 ? 8 : 4)) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
             T s = buf[j];

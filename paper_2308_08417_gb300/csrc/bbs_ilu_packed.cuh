@@ -460,10 +460,15 @@ __global__ void __launch_bounds__(32, packed_cg_min_blocks(R))
     ilu_pattern_stage(Pt, ilu_schedule(sched, P.n), P.row_ptrs,
                       raw + (size_t)S * P.slice, lane);
     const double* vals = P.values + (size_t)sys * P.vps;
-    for (size_t i = tm.tid; i < cells; i += L) {
+#pragma unroll 4
+    for (size_t i = tm.tid; i < cells; i += L) {  // 8-byte asynchronous gathers into ELL order
         const int src = ldg(P.xsrc + i);
-        lu[i] = src >= 0 ? ldg(vals + src) : 0.0;
+        if (src >= 0)
+            cp_async8(lu + i, vals + src);
+        else
+            lu[i] = 0.0;
     }
+    cp_async_wait_all();
     __syncwarp();
     const SysIO io = sys_io(P, sys);
     if (ldg(P.xflag) != 0) {  // a row longer than the table: every system reports NAN

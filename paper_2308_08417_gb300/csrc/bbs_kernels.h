@@ -28,6 +28,9 @@ BBS_DECL(cg)
 BBS_DECL(gmres)
 BBS_DECL(refine)
 #undef BBS_DECL
+// Mixed-mode refinement on ELL with staged values, ELL width K in {3, 5, 7, 9}
+// fixed at compile time, R = 1..4; nullptr for other (R, K).
+const void* refine_ell_fn(int R, int K);
 
 // Packed BiCGSTAB, CG and GMRES (32 / L systems per warp): L = 4, 8 or 16
 // lanes per system, R = 1..kMaxPackedR rows per lane.

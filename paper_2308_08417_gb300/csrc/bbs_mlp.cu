@@ -299,15 +299,55 @@ __global__ void init_kernel(size_t count, float* __restrict__ p, uint64_t seed, 
     }
 }
 
+// x0 = x_prev + gamma * (predicted change), the change de-standardised.
 __global__ void predict_epilogue_kernel(int num_batch, int n, const float* __restrict__ out,
                                         const double* __restrict__ xp, const float* __restrict__ mean,
-                                        const float* __restrict__ stdv, double* __restrict__ x0) {
+                                        const float* __restrict__ stdv, const double* __restrict__ gamma,
+                                        double* __restrict__ x0) {
     const size_t total = (size_t)num_batch * n;
+    const double g = *gamma;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(i % n);
-        x0[i] = xp[i] + (double)out[i] * (double)stdv[3 * n + k] + (double)mean[3 * n + k];
+        x0[i] = xp[i] + g * ((double)out[i] * (double)stdv[3 * n + k] + (double)mean[3 * n + k]);
     }
+}
+
+// Gate statistics of one time step: sums over the batch of c.d and c.c, with
+// c the predicted change (de-standardised network output) and d the true
+// change x_next - x_prev, accumulated in FP64 (acc[0], acc[1]).
+__global__ void gate_observe_kernel(int num_batch, int n, const float* __restrict__ out,
+                                    const double* __restrict__ xp, const double* __restrict__ xn,
+                                    const float* __restrict__ mean, const float* __restrict__ stdv,
+                                    double* __restrict__ acc) {
+    const size_t total = (size_t)num_batch * n;
+    double cd = 0.0, cc = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i % n);
+        const double c = (double)out[i] * (double)stdv[3 * n + k] + (double)mean[3 * n + k];
+        cd += c * (xn[i] - xp[i]);
+        cc += c * c;
+    }
+    for (int m = 16; m; m >>= 1) {
+        cd += __shfl_xor_sync(0xffffffffu, cd, m);
+        cc += __shfl_xor_sync(0xffffffffu, cc, m);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc, cd);
+        atomicAdd(acc + 1, cc);
+    }
+}
+
+// gamma = acc[0] / acc[1], the least-squares scale of the predicted change,
+// limited to [0, 1]; 0 when no change was predicted. Clears the sums.
+__global__ void gate_finalize_kernel(double* __restrict__ acc, double* __restrict__ gamma) {
+    const double num = acc[0], den = acc[1];
+    double g = den > 0.0 ? num / den : 0.0;
+    g = isfinite(g) ? fmin(fmax(g, 0.0), 1.0) : 0.0;
+    *gamma = g;
+    acc[0] = 0.0;
+    acc[1] = 0.0;
 }
 
 }  // namespace mlp
@@ -342,6 +382,7 @@ struct bbs_mlp {
     __nv_bfloat16* DZT[3] = {};
     int32_t* idx = nullptr;
     int* err = nullptr;     // set by a tensor-core GEMM whose waits ran out
+    double* gate = nullptr;  // [gamma, sum c.d, sum c.c] (see bbs_mlp_gate_observe)
     float* part = nullptr;  // split-K partial sums of the weight-gradient GEMMs
     size_t part_cap = 0;    // floats
     int sms = 0;
@@ -590,7 +631,7 @@ bbs_status bbs_mlp_create(bbs_handle* h, int32_t n, int32_t hidden, uint64_t see
     ok = ok && dev_alloc(m, &m->X, MB * m->in_pad) && dev_alloc(m, &m->XT, MB * m->in_pad) &&
          dev_alloc(m, &m->T, MB * n) && dev_alloc(m, &m->out, MB * n) &&
          dev_alloc(m, &m->D, MB * m->n_pad) && dev_alloc(m, &m->DT, MB * m->n_pad) &&
-         dev_alloc(m, &m->idx, MB) && dev_alloc(m, &m->err, 1);
+         dev_alloc(m, &m->idx, MB) && dev_alloc(m, &m->err, 1) && dev_alloc(m, &m->gate, 3);
     for (int l = 0; l < 3 && ok; ++l)
         ok = dev_alloc(m, &m->Z[l], MB * hidden) && dev_alloc(m, &m->Y[l], MB * hidden) &&
              dev_alloc(m, &m->YT[l], MB * hidden) && dev_alloc(m, &m->DZ[l], MB * hidden) &&
@@ -618,6 +659,8 @@ bbs_status bbs_mlp_create(bbs_handle* h, int32_t n, int32_t hidden, uint64_t see
     std::vector<float> ones(F, 1.0f);
     cudaMemcpy(m->inv_std, ones.data(), F * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(m->stdv, ones.data(), F * sizeof(float), cudaMemcpyHostToDevice);
+    const double gamma_one = 1.0;  // ungated until bbs_mlp_gate_finalize
+    cudaMemcpy(m->gate, &gamma_one, sizeof(double), cudaMemcpyHostToDevice);
     pack_all(m, nullptr);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -804,6 +847,29 @@ bbs_status bbs_mlp_forward(bbs_mlp* m, const uint16_t* feats, int32_t M, float* 
     return BBS_OK;
 }
 
+}  // extern "C"
+
+// The network over a batch, max_batch rows at a time; `tail(r0, rows)`
+// consumes each piece's output in m->out.
+template <class Tail>
+static bbs_status run_batch(bbs_mlp* m, const bbs_batch_matrix* A, const double* b, const double* x_prev,
+                            cudaStream_t st, Tail tail) {
+    const int n = m->n;
+    for (int r0 = 0; r0 < A->num_batch; r0 += m->max_batch) {
+        const int rows = std::min(m->max_batch, A->num_batch - r0);
+        bbs::mlp::samples_kernel<<<rows, 128, 0, st>>>(
+            rows, n, m->in_pad, A->row_ptrs, A->col_idxs, A->values + (size_t)r0 * A->nnz, A->nnz,
+            b + (size_t)r0 * n, x_prev + (size_t)r0 * n, nullptr, m->mean, m->inv_std, m->X, nullptr);
+        cudaError_t e = forward(m, m->X, rows, false, st);
+        if (e != cudaSuccess) return errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
+        tail(r0, rows);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BBS_OK : errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
+}
+
+extern "C" {
+
 bbs_status bbs_mlp_predict(bbs_mlp* m, const bbs_batch_matrix* A, const double* b, const double* x_prev,
                            double* x0, void* stream) {
     if (m == nullptr || !b || !x_prev || !x0) return errf(BBS_ERR_INVALID_ARG, "null argument");
@@ -811,18 +877,35 @@ bbs_status bbs_mlp_predict(bbs_mlp* m, const bbs_batch_matrix* A, const double* 
     if (s != BBS_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int n = m->n;
-    for (int r0 = 0; r0 < A->num_batch; r0 += m->max_batch) {
-        const int rows = std::min(m->max_batch, A->num_batch - r0);
-        bbs::mlp::samples_kernel<<<rows, 128, 0, st>>>(
-            rows, n, m->in_pad, A->row_ptrs, A->col_idxs, A->values + (size_t)r0 * A->nnz, A->nnz,
-            b + (size_t)r0 * n,
-            x_prev + (size_t)r0 * n, nullptr, m->mean, m->inv_std, m->X, nullptr);
-        cudaError_t e = forward(m, m->X, rows, false, st);
-        if (e != cudaSuccess) return errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
+    return run_batch(m, A, b, x_prev, st, [&](int r0, int rows) {
         bbs::mlp::predict_epilogue_kernel<<<std::min((rows * n + 255) / 256, 4096), 256, 0, st>>>(
-            rows, n, m->out, x_prev + (size_t)r0 * n, m->mean, m->stdv, x0 + (size_t)r0 * n);
-    }
+            rows, n, m->out, x_prev + (size_t)r0 * n, m->mean, m->stdv, m->gate, x0 + (size_t)r0 * n);
+    });
+}
+
+bbs_status bbs_mlp_gate_observe(bbs_mlp* m, const bbs_batch_matrix* A, const double* b, const double* x_prev,
+                                const double* x_next, void* stream) {
+    if (m == nullptr || !b || !x_prev || !x_next) return errf(BBS_ERR_INVALID_ARG, "null argument");
+    bbs_status s = check_csr_batch(m, A);
+    if (s != BBS_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int n = m->n;
+    return run_batch(m, A, b, x_prev, st, [&](int r0, int rows) {
+        bbs::mlp::gate_observe_kernel<<<std::min((rows * n + 255) / 256, 1024), 256, 0, st>>>(
+            rows, n, m->out, x_prev + (size_t)r0 * n, x_next + (size_t)r0 * n, m->mean, m->stdv, m->gate + 1);
+    });
+}
+
+bbs_status bbs_mlp_gate_finalize(bbs_mlp* m, void* stream) {
+    if (m == nullptr) return errf(BBS_ERR_INVALID_ARG, "null argument");
+    bbs::mlp::gate_finalize_kernel<<<1, 1, 0, reinterpret_cast<cudaStream_t>(stream)>>>(m->gate + 1, m->gate);
     cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BBS_OK : errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
+}
+
+bbs_status bbs_mlp_get_gate(bbs_mlp* m, double* gamma) {
+    if (m == nullptr || gamma == nullptr) return errf(BBS_ERR_INVALID_ARG, "null argument");
+    cudaError_t e = cudaMemcpy(gamma, m->gate, sizeof(double), cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? BBS_OK : errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
 }
 

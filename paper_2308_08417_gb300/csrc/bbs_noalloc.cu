@@ -1,13 +1,13 @@
 // bbs_solve_noalloc: the solve for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that records its work into a CUDA
-// graph under stream capture (allocation is not a capturable operation),
-// latency-critical loops that must not hit the allocator, and hosts that embed
-// this library under a memory budget or a pool they manage themselves. For
-// them the scratch the solve needs (today: the FP32 copy of the values in the
-// mixed-precision mode, and the GMRES basis when it does not fit in shared
-// memory) comes from a fixed array compiled into the library instead of a
-// caller-provided workspace.
+// Some callers cannot call cudaMalloc: hosts whose device memory is already
+// reserved by another allocator (a framework's caching pool, a server's
+// arena, a fixed budget), and loops that must not wait on the allocator
+// (cudaFree synchronises the device, and a cudaMalloc can stall other
+// streams). For them the scratch the solve needs (the FP32 copy of the values
+// in the mixed-precision mode when they are not staged in shared memory, the
+// GMRES basis when it does not fit there) comes from a fixed array compiled
+// into the library instead of a caller-provided workspace.
 //
 // The array is a file-scope static __device__ buffer of kScratchBytes bytes.
 // Every GPU that loads the library holds it until the process exits. Host
@@ -15,9 +15,10 @@
 // a stand-in), so the first call on each device, with that device current,
 // looks the address up with cudaGetSymbolAddress and caches it; that first
 // call should therefore come before any stream capture. All calls share the
-// one array: calls that overlap on the GPU (different streams, or different
-// host threads) race on it and must be serialised by the caller. The solve
-// overwrites every scratch byte it reads, so no clearing is needed.
+// one array and it keeps the last call's contents: calls that overlap on the
+// GPU (different streams, or different host threads) race on it and must be
+// serialised by the caller. The solve writes every scratch byte before it
+// reads it, so nothing needs clearing between calls.
 #include <cstdio>
 #include <mutex>
 
@@ -80,21 +81,29 @@ extern "C" bbs_status bbs_solve_noalloc(bbs_handle* handle, const bbs_batch_matr
     if (need <= kScratchBytes)
         return bbs_solve(handle, A, b, x, opts, log, scratch, kScratchBytes, stream);
 
-    // Scratch grows linearly with the number of systems: solve in chunks of
-    // systems whose scratch fits, one after the other on the stream.
-    bbs_batch_matrix one = *A;
-    one.num_batch = 1;
-    size_t per = 0;
-    if ((s = bbs_workspace_size(handle, &one, opts, &per)) != BBS_OK) return s;
-    if (per > kScratchBytes) {
+    // Scratch grows linearly with the number of systems, plus parts that do
+    // not (the packed-CSR tables, the ILU(0) schedule): size the chunks from
+    // the marginal bytes of one more system, then solve them one after the
+    // other on the stream.
+    bbs_batch_matrix probe = *A;
+    size_t one = 0, two = 0;
+    probe.num_batch = 1;
+    if ((s = bbs_workspace_size(handle, &probe, opts, &one)) != BBS_OK) return s;
+    if (one > kScratchBytes) {
         char msg[256];
         snprintf(msg, sizeof msg,
                  "one system needs %zu bytes of scratch; the static scratch holds %zu bytes",
-                 per, kScratchBytes);
+                 one, kScratchBytes);
         return bbs::record_error(BBS_ERR_UNSUPPORTED, msg);
     }
-    int chunk = (int)(kScratchBytes / per);
-    for (;;) {  // the per-system size is rounded up per buffer: shrink until it fits
+    probe.num_batch = 2;
+    if ((s = bbs_workspace_size(handle, &probe, opts, &two)) != BBS_OK) return s;
+    const size_t per = two > one ? two - one : 1;
+    const size_t fixed = one > per ? one - per : 0;
+    size_t est = (kScratchBytes - fixed) / per;
+    if (est > (size_t)A->num_batch) est = (size_t)A->num_batch;
+    int chunk = est < 1 ? 1 : (int)est;
+    for (;;) {  // every buffer is rounded up on its own: shrink until it fits
         bbs_batch_matrix c = *A;
         c.num_batch = chunk;
         size_t cneed = 0;

@@ -777,12 +777,17 @@ struct PackedGroup {
         const double* vals = P.values + (size_t)sys * P.vps;
         double* as = reinterpret_cast<double*>(slice + P.stage_off);
         op.A = Mat<double>{vals, P.row_ptrs, P.cols, P.n, P.k};
-        if constexpr (FMT == FMT_CSR) {
+        if constexpr (FMT == FMT_CSR) {  // gathered into ELL order by 8-byte asynchronous copies
             const int count = P.xk * P.n;
+#pragma unroll 4
             for (int i = tm.tid; i < count; i += L) {
                 const int src = ldg(P.xsrc + i);
-                as[i] = src >= 0 ? ldg(vals + src) : 0.0;
+                if (src >= 0)
+                    cp_async8(as + i, vals + src);
+                else
+                    as[i] = 0.0;
             }
+            cp_async_wait_all();
             op.S = Mat<double>{as, nullptr, P.xcols, P.n, P.xk};
         } else {
             stage_values(vals, as, P.vps, tm);

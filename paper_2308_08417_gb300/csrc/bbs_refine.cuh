@@ -15,8 +15,8 @@ namespace bbs {
 // FP32 BiCGSTAB from d = 0 on A32 d = w; stops when the recursive residual
 // passes inner_tol*||w||, on a breakdown or non-finite scalar, or after
 // max_inner iterations. Returns the iteration at which it stopped.
-template <int FMT, int R>
-__device__ __forceinline__ int inner_bicgstab32(const Op<FMT, R, float, float>& op,
+template <int R, class Op32>
+__device__ __forceinline__ int inner_bicgstab32(const Op32& op,
                                                 const float (&dinv)[R], const float (&w)[R],
                                                 float (&d)[R], float inner_tol, int max_inner,
                                                 float* xa, float* xb, float* red, int& parity,
@@ -106,48 +106,90 @@ __device__ __forceinline__ void stage_values_rounded(const double* __restrict__ 
     for (size_t j = i + tm.tid; j < count; j += tm.nt) s[j] = (float)ldg(g + j);
 }
 
-// Shared memory: red64[256] | xd[n_pad] (FP64) | red32[256] | xa[n_pad] |
-// xb[n_pad] (FP32) | staged FP32 values (optional)
-template <int FMT, int R>
-__global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const SolveParams P) {
-    extern __shared__ __align__(16) unsigned char raw[];
-    const Team tm = Team::block();
-    const int sys = blockIdx.x;
-    const int n = P.n;
-    const SysIO io = sys_io(P, sys);
-    double* red64 = reinterpret_cast<double*>(raw);
-    double* xd = red64 + 256;
-    float* red32 = reinterpret_cast<float*>(xd + P.n_pad);
-    float* xa = red32 + 256;
-    float* xb = xa + P.n_pad;
-    int par64 = 0, par32 = 0;
-
-    const Mat<double> A64{P.values + (size_t)sys * P.vps, P.row_ptrs, P.cols, n, P.k};
-    const Op<FMT, R, double, double> op64{A64, nullptr};
-    // Without an FP32 copy (values32 == nullptr, only when the values are
-    // staged) the block rounds the FP64 values to FP32 as it stages them.
-    const bool copy32 = P.values32 != nullptr;
-    const Mat<float> A32{copy32 ? P.values32 + (size_t)sys * P.vps : nullptr, P.row_ptrs, P.cols, n, P.k};
-    const float* as = nullptr;
-    if (P.stage) {
-        float* s = reinterpret_cast<float*>(raw + P.stage_off);
-        if (copy32)
-            stage_values(A32.vals, s, P.vps, tm);
-        else
-            stage_values_rounded(A64.vals, s, P.vps, tm);
-        tm.sync();
-        as = s;
+// Staged FP32 ELL values as (value, column) pairs in each thread's own
+// order: pair (q k + j) nt + t holds slot j of row t + q nt, so one 8-byte
+// shared-memory load gives a slot's value and column and consecutive threads
+// read consecutive pairs. Padding slots and rows past n carry value 0 and
+// column n, a zero kept after the end of every FP32 SpMV input vector, so the
+// SpMV has no branch. The values are the FP32 copy's, or the FP64 values
+// rounded to nearest as they are staged.
+template <int R>
+__device__ __forceinline__ void stage_pairs_ell(const double* __restrict__ g64, const float* __restrict__ g32,
+                                                const int32_t* __restrict__ cols, float2* __restrict__ pairs,
+                                                int n, int k, const Team& tm) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        for (int j = 0; j < k; ++j) {
+            float v = 0.0f;
+            int c = n;
+            if (row < n) {
+                const size_t i = (size_t)j * n + row;
+                const int cc = ldg(cols + i);
+                if (cc >= 0) {
+                    c = cc;
+                    v = g32 != nullptr ? ldg(g32 + i) : (float)ldg(g64 + i);
+                }
+            }
+            pairs[(size_t)(q * k + j) * tm.nt + tm.tid] = make_float2(v, __int_as_float(c));
+        }
     }
-    const Op<FMT, R, float, float> op32{A32, as};
+}
 
+// y = A x over the staged pairs (slots in ascending column order, FMA).
+// K > 0 fixes the ELL width at compile time (the multi-level dispatch of
+// Sec. 3.3 applied to the stencil width): the slot loop then unrolls fully,
+// every pair sits at a constant multiple of the thread stride, and the R
+// rows' FMA chains interleave. K = 0 takes the width k at run time.
+template <int R, int K = 0>
+struct PairOp32 {
+    const float2* __restrict__ pairs;
+    int k;
+    __device__ __forceinline__ void apply(const float* __restrict__ xs, float (&y)[R], const Team& tm) const {
+        const float2* p = pairs + tm.tid;
+        if constexpr (K > 0) {
+            const int nt = tm.nt;
+            float sum[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) sum[q] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const float2 e = p[(q * K + j) * nt];
+                    sum[q] = fmaf(e.x, xs[__float_as_int(e.y)], sum[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) y[q] = sum[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                float sum = 0.0f;
+#pragma unroll 3
+                for (int j = 0; j < k; ++j) {
+                    const float2 e = *p;
+                    p += tm.nt;
+                    sum = fmaf(e.x, xs[__float_as_int(e.y)], sum);
+                }
+                y[q] = sum;
+            }
+        }
+    }
+};
+
+// The refinement loop of one system: r = b - A x in FP64, exit test, FP32
+// inner solve for the correction direction d, x += ||r|| d in FP64.
+template <int FMT, int R, class Op32>
+__device__ __forceinline__ void refine_system(const SolveParams& P, const SysIO& io,
+                                              const Op<FMT, R, double, double>& op64, const Op32& op32,
+                                              const float (&dinv)[R], double* red64, double* xd, float* red32,
+                                              float* xa, float* xb, const Team& tm) {
+    const int n = P.n;
+    int par64 = 0, par32 = 0;
     double b[R], x[R], r[R];
-    float dinv[R], w[R], d[R];
+    float w[R], d[R];
     load_system<R>(io, b, x, tm);
-    if (copy32)
-        jacobi_setup<FMT, R>(A32, P.precond == 1, dinv, tm);
-    else  // 1 / a_ii in FP32 of the FP32-rounded diagonal, as from a copy
-        jacobi_setup<FMT, R>(A64, P.precond == 1, dinv, tm);
-
     double s0[1] = {pdot(b, b)};
     block_sum(s0, red64, par64, tm);
     const double nb2 = s0[0];
@@ -173,12 +215,68 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const Sol
         const double rinv = 1.0 / rn;
 #pragma unroll
         for (int q = 0; q < R; ++q) w[q] = (float)(r[q] * rinv);
-        inner_total += inner_bicgstab32(op32, dinv, w, d, (float)P.inner_tol, P.max_iters, xa, xb,
-                                        red32, par32, tm, n);
+        inner_total += inner_bicgstab32<R>(op32, dinv, w, d, (float)P.inner_tol, P.max_iters, xa, xb, red32,
+                                           par32, tm, n);
 #pragma unroll
         for (int q = 0; q < R; ++q) x[q] = fma(rn, (double)d[q], x[q]);
     }
     write_result(io, x, status, k, sqrt(rr / nb2), inner_total, tm);
+}
+
+// Shared memory: red64[256] | xd[n_pad] (FP64) | red32[256] | xa[n_pad + 2] |
+// xb[n_pad + 2] (FP32; entry n stays 0) | staged FP32 values or ELL pairs
+// (optional). K > 0 (ELL with staged values only): the pair SpMV for an ELL
+// width of exactly K.
+template <int FMT, int R, int K = 0>
+__global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const SolveParams P) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    const Team tm = Team::block();
+    const int sys = blockIdx.x;
+    const int n = P.n;
+    const SysIO io = sys_io(P, sys);
+    double* red64 = reinterpret_cast<double*>(raw);
+    double* xd = red64 + 256;
+    float* red32 = reinterpret_cast<float*>(xd + P.n_pad);
+    float* xa = red32 + 256;
+    float* xb = xa + P.n_pad + 2;
+
+    const Mat<double> A64{P.values + (size_t)sys * P.vps, P.row_ptrs, P.cols, n, P.k};
+    const Op<FMT, R, double, double> op64{A64, nullptr};
+    // Without an FP32 copy (values32 == nullptr, only when the values are
+    // staged) the block rounds the FP64 values to FP32 as it stages them.
+    const bool copy32 = P.values32 != nullptr;
+    const Mat<float> A32{copy32 ? P.values32 + (size_t)sys * P.vps : nullptr, P.row_ptrs, P.cols, n, P.k};
+    float dinv[R];
+    if (copy32)
+        jacobi_setup<FMT, R>(A32, P.precond == 1, dinv, tm);
+    else  // 1 / a_ii in FP32 of the FP32-rounded diagonal, as from a copy
+        jacobi_setup<FMT, R>(A64, P.precond == 1, dinv, tm);
+    if (tm.tid == 0) {
+        xa[n] = 0.0f;
+        xb[n] = 0.0f;
+    }
+    if constexpr (FMT == FMT_ELL) {
+        if (P.stage) {
+            float2* pairs = reinterpret_cast<float2*>(raw + P.stage_off);
+            stage_pairs_ell<R>(A64.vals, A32.vals, P.cols, pairs, n, P.k, tm);
+            tm.sync();
+            const PairOp32<R, K> op32{pairs, P.k};
+            refine_system<FMT, R>(P, io, op64, op32, dinv, red64, xd, red32, xa, xb, tm);
+            return;
+        }
+    }
+    const float* as = nullptr;
+    if (P.stage) {
+        float* s = reinterpret_cast<float*>(raw + P.stage_off);
+        if (copy32)
+            stage_values(A32.vals, s, P.vps, tm);
+        else
+            stage_values_rounded(A64.vals, s, P.vps, tm);
+        as = s;
+    }
+    tm.sync();
+    const Op<FMT, R, float, float> op32{A32, as};
+    refine_system<FMT, R>(P, io, op64, op32, dinv, red64, xd, red32, xa, xb, tm);
 }
 
 // FP32 copy of the values for the mixed mode (when the caller gives none).

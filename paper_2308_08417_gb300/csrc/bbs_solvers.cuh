@@ -135,7 +135,8 @@ __device__ __forceinline__ void load_system(const SysIO& io, double (&b)[R], dou
     }
 }
 
-__device__ __forceinline__ double quiet_nan() { return quiet_nan(); }
+// The default quiet NaN (sign 0, exponent all ones, top fraction bit set).
+__device__ __forceinline__ double quiet_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
 
 // The system's values, staged in shared memory at `stage` when non-null.
 template <int FMT, int R>

@@ -3,15 +3,18 @@
 A_i(t) = A_i + 0.01 t B_i and b_i(t) = b_i + 0.01 t c_i (workloads.TimeSeries)
 are solved step after step; each step's solve starts from an initial guess.
 The baseline guess is the previous solution x(t-1). The learned guess is
-x(t-1) plus the change an MLP predicts from (diag A(t), b(t), x(t-1)); the
-network is trained on the changes the solver produced in the first steps.
+x(t-1) plus gamma times the change an MLP predicts from (diag A(t), b(t),
+x(t-1)); the network is trained on the changes the solver produced in the
+first steps, and the gate gamma in [0, 1] is the least-squares scale of its
+prediction on the last training steps, which the network does not train on.
 
 Every step of the method runs in libbbs.so: the solves (bbs_solve), the
 input statistics (bbs_mlp_observe / bbs_mlp_finalize_stats), the training
 samples (bbs_mlp_make_samples), the forward/backward passes and Adam
-(bbs_mlp_train_step) and the prediction (bbs_mlp_predict). This module only
-builds each step's inputs (an elementwise A + 0.01 t B on the device) and
-sequences the calls.
+(bbs_mlp_train_step), the gate (bbs_mlp_gate_observe / bbs_mlp_gate_finalize)
+and the prediction (bbs_mlp_predict). This module only builds each step's
+inputs (an elementwise A + 0.01 t B on the device), sequences the calls and
+tallies the report.
 """
 
 from __future__ import annotations
@@ -38,6 +41,7 @@ class StepRecord:
     converged: int = 0
     iters_zero: float = 0.0
     ms_zero: float = 0.0
+    ms_predict: float = 0.0
 
 
 @dataclass
@@ -49,6 +53,10 @@ class LearnedReport:
     collect_s: float
     losses: list = field(default_factory=list)
     records: list = field(default_factory=list)
+    gate: float = 1.0
+    gate_steps: int = 0
+    gate_err_learned: float = 0.0
+    gate_err_base: float = 0.0
 
     def summary(self) -> dict:
         r = self.records
@@ -70,6 +78,11 @@ class LearnedReport:
             "train_s": self.train_s, "collect_s": self.collect_s,
             "final_loss": self.losses[-1] if self.losses else None,
             "first_loss": self.losses[0] if self.losses else None,
+            "predict_ms_per_step": float(np.mean([x.ms_predict for x in r])),
+            "solve_ms_per_step_base": base_ms / len(r),
+            "gate": self.gate, "gate_steps": self.gate_steps,
+            "gate_steps_error_ratio": (self.gate_err_learned / self.gate_err_base
+                                       if self.gate_err_base > 0 else None),
         }
 
 
@@ -116,8 +129,15 @@ class TimeStepped:
         self.h.solve(self.matrix(), self.rhs, y, o, lg)
         return float(lg.rel_res.mean())
 
-    def run(self, train_steps=64, eval_steps=16, epochs=6, lr=1e-3, batch=4096, progress=None) -> LearnedReport:
+    def run(self, train_steps=64, eval_steps=16, epochs=6, lr=1e-3, batch=4096, progress=None,
+            gate_steps=8) -> LearnedReport:
+        """Solve steps 0..train_steps-1 from x(t-1); train the network on the
+        changes of steps 1..train_steps-gate_steps-1; fit the gate on the last
+        gate_steps training steps (held out from the network's training); then
+        time eval_steps steps of (prediction + solve) against a solve from
+        x(t-1) and one from x0 = 0."""
         Bsz, n = self.ts.num_batch, self.n
+        fit_end = train_steps - gate_steps  # samples of steps 1..fit_end-1
         # 1. solve the training steps from the previous solution; keep x(t)
         t0 = time.perf_counter()
         xs = [torch.zeros(Bsz, n, dtype=torch.float64, device=self.dev)]  # x(-1) = 0
@@ -130,14 +150,14 @@ class TimeStepped:
         collect_s = time.perf_counter() - t0
         # 2. statistics and samples from steps 1..train_steps-1 (x(t-1) from the solver)
         t1 = time.perf_counter()
-        for t in range(1, train_steps):
+        for t in range(1, fit_end):
             self.set_step(t)
             self.mlp.observe(self.matrix(), self.rhs, xs[t], xs[t + 1])
         self.mlp.finalize_stats()
-        S = (train_steps - 1) * Bsz
+        S = (fit_end - 1) * Bsz
         feats = torch.empty(S, self.mlp.in_pad, dtype=torch.bfloat16, device=self.dev)
         targets = torch.empty(S, n, dtype=torch.float32, device=self.dev)
-        for k, t in enumerate(range(1, train_steps)):
+        for k, t in enumerate(range(1, fit_end)):
             self.set_step(t)
             self.mlp.make_samples(self.matrix(), self.rhs, xs[t], xs[t + 1],
                                   feats[k * Bsz:(k + 1) * Bsz], targets[k * Bsz:(k + 1) * Bsz])
@@ -162,8 +182,21 @@ class TimeStepped:
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t1
         del feats, targets
-        # 4. evaluation steps: same x(t-1) for both guesses
         rep = LearnedReport(train_steps, eval_steps, Bsz, train_s, collect_s, losses)
+        # 4. the gate, fitted on the held-out training steps; the squared
+        # error of the gated guess there against that of x(t-1)
+        if gate_steps > 0:
+            for t in range(fit_end, train_steps):
+                self.set_step(t)
+                self.mlp.gate_observe(self.matrix(), self.rhs, xs[t], xs[t + 1])
+            self.mlp.gate_finalize()
+            rep.gate, rep.gate_steps = self.mlp.gate(), gate_steps
+            for t in range(fit_end, train_steps):
+                self.set_step(t)
+                x0 = self.mlp.predict(self.matrix(), self.rhs, xs[t])
+                rep.gate_err_learned += float(((xs[t + 1] - x0) ** 2).sum())
+                rep.gate_err_base += float(((xs[t + 1] - xs[t]) ** 2).sum())
+        # 5. evaluation steps: same x(t-1) for every guess
         x_prev = xs[-1]
         del xs
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -199,6 +232,6 @@ class TimeStepped:
             torch.cuda.synchronize()
             ms_z = e0.elapsed_time(e1)
             it_z = float(self.log.iters.double().mean())
-            rep.records.append(StepRecord(t, it_b, it_l, ms_b, ms_l, r0b, r0l, conv, it_z, ms_z))
+            rep.records.append(StepRecord(t, it_b, it_l, ms_b, ms_l, r0b, r0l, conv, it_z, ms_z, ms_p))
             x_prev = xl
         return rep

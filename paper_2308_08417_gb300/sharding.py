@@ -19,6 +19,31 @@ def shard_range(num_batch: int, rank: int, world: int) -> tuple[int, int]:
     return begin, begin + base + (1 if rank < extra else 0)
 
 
+def cost_shard_range(costs, rank: int, world: int) -> tuple[int, int]:
+    """[begin, end) of a contiguous split of systems with per-system cost
+    estimates `costs` (uneven batches): boundary r is the first system whose
+    cumulative cost reaches r / world of the total, so every rank gets about
+    the same work. Covers every system exactly once; with equal costs it
+    matches shard_range up to rounding."""
+    import numpy as np
+
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    c = np.asarray(costs, dtype=np.float64)
+    if c.ndim != 1 or (c < 0).any():
+        raise ValueError("costs must be a 1-D array of non-negative numbers")
+    total = np.concatenate([[0.0], np.cumsum(c)])
+
+    def cut(r):
+        if r <= 0:
+            return 0
+        if r >= world:
+            return len(c)
+        return int(np.searchsorted(total, total[-1] * r / world, side="left"))
+
+    return cut(rank), cut(rank + 1)
+
+
 def max_over_ranks(value: float, dist=None, device=None) -> float:
     """The largest `value` over all ranks (the job's time is its slowest rank's)."""
     if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:

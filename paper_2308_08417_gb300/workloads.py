@@ -333,6 +333,20 @@ class VarBatch:
         return (pat_n, pat_nnz, rp_off, ci_off,
                 np.concatenate(rps).astype(np.int32), np.concatenate(cis).astype(np.int32))
 
+    def slice(self, begin: int, end: int) -> "VarBatch":
+        """Systems [begin, end) as a batch of their own (views of the values
+        and vectors, offsets re-based; the pattern pool is kept whole)."""
+        if not 0 <= begin <= end <= self.num_batch:
+            raise ValueError("need 0 <= begin <= end <= num_batch")
+        nnz, nn = self.sys_nnz().astype(np.int64), self.sys_n().astype(np.int64)
+        v0 = int(self.val_off[begin]) if begin < self.num_batch else self.values.size
+        x0 = int(self.vec_off[begin]) if begin < self.num_batch else self.b.size
+        v1 = v0 + int(nnz[begin:end].sum())
+        x1 = x0 + int(nn[begin:end].sum())
+        return VarBatch(self.patterns, self.sys_pattern[begin:end], self.val_off[begin:end] - v0,
+                        self.vec_off[begin:end] - x0, self.values[v0:v1], self.b[x0:x1], self.x0[x0:x1],
+                        f"{self.name}[{begin}:{end}]")
+
     def system(self, i: int):
         """(pattern, values[nnz], b[n], x0[n]) of system i (views)."""
         p = self.patterns[int(self.sys_pattern[i])]

@@ -143,3 +143,42 @@ def test_learned_guess_pipeline(bbs):
     assert all(r.converged == 2048 for r in rep.records)
     assert s["final_loss"] < s["first_loss"]
     assert np.isfinite(s["init_residual_learned"]) and np.isfinite(s["iters_learned"])
+    # on the held-out training steps the gated guess is no worse than x(t-1)
+    assert 0.0 <= s["gate"] <= 1.0 and s["gate_steps"] == 8
+    assert s["gate_steps_error_ratio"] <= 1.0 + 1e-9
+
+
+def test_gate_is_the_least_squares_scale(bbs):
+    """The gate gamma is sum c.d / sum c.c over the observed steps (c the
+    predicted change, d the true one), limited to [0, 1]; with it the guess's
+    squared error over those steps is at most that of x0 = x(t-1)."""
+    net = bbs.MLP(bbs.Handle(0), N, hidden=HID, seed=5, max_batch=1024)
+    ts = W.time_stepped(num_batch=512, steps=4)
+    dev = "cuda"
+    rng = np.random.default_rng(9)
+    steps = []
+    for t in (1, 2, 3):
+        A = bbs.DeviceBatch.from_batch(W.make_batch(ts.pattern, ts.values_at(t), "csr"), dev)
+        b = torch.as_tensor(ts.rhs_at(t), device=dev)
+        xp = torch.as_tensor(rng.normal(size=(512, N)), device=dev)
+        xn = xp + torch.as_tensor(rng.normal(scale=0.1, size=(512, N)), device=dev)
+        steps.append((A, b, xp, xn))
+    for A, b, xp, xn in steps:  # statistics so that the network's change is not tiny
+        net.observe(A, b, xp, xn)
+    net.finalize_stats()
+    assert net.gate() == 1.0  # ungated before a fit
+    cs = [(net.predict(A, b, xp) - xp) for A, b, xp, _ in steps]
+    for A, b, xp, xn in steps:
+        net.gate_observe(A, b, xp, xn)
+    net.gate_finalize()
+    g = net.gate()
+    num = sum(float((c * (xn - xp)).sum()) for c, (_, _, xp, xn) in zip(cs, steps))
+    den = sum(float((c * c).sum()) for c in cs)
+    want = min(max(num / den, 0.0), 1.0)
+    assert 0.0 <= g <= 1.0 and abs(g - want) <= 1e-9 * max(1.0, abs(want))
+    err_gated = err_prev = 0.0
+    for A, b, xp, xn in steps:
+        x0 = net.predict(A, b, xp)
+        err_gated += float(((xn - x0) ** 2).sum())
+        err_prev += float(((xn - xp) ** 2).sum())
+    assert err_gated <= err_prev * (1 + 1e-12)

@@ -276,9 +276,10 @@ def test_packed_argument_errors(bbs, handle):
                      bbs.bbs_default_options(threads_per_system=4), log)
 
 
-def test_csr_row_longer_than_bound_reports_nan(bbs, handle):
-    """A CSR bound (ell_k) below the longest row: every system reports NAN and
-    x is left alone; the right bound solves them."""
+def test_csr_row_longer_than_bound_is_an_argument_error(bbs, handle):
+    """A CSR bound (ell_k) below the longest row: bbs_solve and bbs_solve_host
+    return BBS_ERR_INVALID_ARG before any launch and x is left alone; the right
+    bound solves the batch."""
     wl = W.tiny_tridiagonal(40)
     A = wl.matrix("csr")
     good = bbs.DeviceBatch.from_batch(A, "cuda")
@@ -290,12 +291,50 @@ def test_csr_row_longer_than_bound_reports_nan(bbs, handle):
         x = x0.clone()
         log = bbs.Log.empty(40)
         o = bbs.bbs_default_options(threads_per_system=tps)
-        handle.solve(bad, b, x, o, log, handle.workspace(bad, o))
+        for _ in range(2):  # the second call answers from the handle's record
+            with pytest.raises(bbs.BBSError) as err:
+                handle.solve(bad, b, x, o, log, handle.workspace(bad, o))
+            assert err.value.status == 1
         torch.cuda.synchronize()
-        assert (log.status.cpu().numpy() == 3).all() and (log.iters.cpu().numpy() == 0).all()
         assert torch.equal(x, x0)
         g = gpu_solve(bbs, handle, A, wl.b, threads_per_system=tps)
         assert (g[3] == 0).all()
+    hbad = bbs.DeviceBatch("csr", good.n, good.nnz, 2, good.row_ptrs.cpu(), good.col_idxs.cpu(),
+                           good.values.cpu())
+    hx = x0.cpu()
+    with pytest.raises(bbs.BBSError) as err:
+        handle.solve_host(hbad, b.cpu(), hx, bbs.bbs_default_options(threads_per_system=4),
+                          bbs.Log.empty(40, device="cpu"))
+    assert err.value.status == 1 and torch.equal(hx, x0.cpu())
+
+
+def test_csr_pattern_rewritten_in_place_reports_nan(bbs, handle):
+    """The device-side guard behind the handle's record: a pattern checked once
+    and then rewritten in place (same address, n, nnz and bound) with a row
+    longer than the bound makes every system report NAN, x untouched."""
+    wl = W.tiny_tridiagonal(40)
+    A = wl.matrix("csr")
+    dA = bbs.DeviceBatch.from_batch(A, "cuda")
+    b = torch.as_tensor(wl.b, device="cuda")
+    o = bbs.bbs_default_options(threads_per_system=8)
+    x = torch.zeros_like(b)
+    log = bbs.Log.empty(40)
+    handle.solve(dA, b, x, o, log, handle.workspace(dA, o))  # the pattern is checked and remembered
+    torch.cuda.synchronize()
+    assert (log.status.cpu().numpy() == 0).all()
+    # same n = 32 and nnz = 94: row 0 holds columns 0..3, row 1 only its diagonal
+    n = A.n
+    rows = [[0, 1, 2, 3], [1]] + [[i - 1, i, i + 1] for i in range(2, n - 1)] + [[n - 2, n - 1]]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    assert rp[-1] == A.nnz
+    dA.row_ptrs.copy_(torch.as_tensor(rp))
+    dA.col_idxs.copy_(torch.as_tensor(np.concatenate(rows).astype(np.int32)))
+    x0 = torch.full_like(b, 0.25)
+    x = x0.clone()
+    handle.solve(dA, b, x, o, log, handle.workspace(dA, o))
+    torch.cuda.synchronize()
+    assert (log.status.cpu().numpy() == 3).all() and (log.iters.cpu().numpy() == 0).all()
+    assert torch.equal(x, x0)
 
 
 def test_host_buffer_chunks_match_the_device_solve(bbs, handle):
