@@ -143,11 +143,16 @@ __device__ __forceinline__ void spmv(const Mat<V>& A, const T* __restrict__ xs, 
                 if (j < len) sum = fma(T(ldg(A.vals + e0 + j)), xs[ldg(A.cols + e0 + j)], sum);
         } else if (row < A.n) {
             if constexpr (FMT == FMT_ELL) {
+                // the value load does not wait for the column test (every
+                // slot of the k*n table exists), so the slots' loads overlap
                 const int32_t* c = A.cols + row;
                 const V* a = A.vals + row;
+#pragma unroll 3
                 for (int j = 0; j < A.k; ++j) {
                     const int col = ldg(c + (size_t)j * A.n);
-                    if (col >= 0) sum = fma(T(ldg(a + (size_t)j * A.n)), xs[col], sum);
+                    const V av = ldg(a + (size_t)j * A.n);
+                    const T prod = col >= 0 ? fma(T(av), xs[col], sum) : sum;
+                    sum = prod;
                 }
             } else {
                 const V* a = A.vals + (size_t)row * A.n;
