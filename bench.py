@@ -64,11 +64,13 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 # without a capture reports null, and an entry is removed when its kernel
 # changes. The uneven batch's entry is the capture of its first 20,000
 # systems; per-system bytes vary with n, so its scaling is approximate.
-TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (134.9e6, 16384),
-           ("bicgstab_folded_kernel", "stencil2d5_12x12"): (280.8e6, 32768),
-           ("cg_packed_kernel", "sym_stencil2d5_12x12_cg+jacobi"): (133.05e6, 16384),
-           ("refine_kernel", "stencil2d9_32x32"): (398.9e6, 4096),
-           ("varsize_kernel", "uneven_n16-1024"): (332.9e6, 20000)}
+TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (134.70e6, 16384),
+           ("bicgstab_folded_kernel", "stencil2d5_12x12"): (280.75e6, 32768),
+           ("cg_packed_kernel", "sym_stencil2d5_12x12_cg+jacobi"): (132.98e6, 16384),
+           ("gmres_packed_kernel", "stencil2d5_12x12_gmres+jacobi"): (223.74e6, 16384),
+           ("bicgstab_ilu_packed_kernel", "stencil2d5_12x12_bicgstab+ilu0"): (134.60e6, 16384),
+           ("refine_kernel", "stencil2d9_32x32"): (397.24e6, 4096),
+           ("varsize_kernel", "uneven_n16-1024"): (333.35e6, 20000)}
 
 
 # mixed refinement of the 32x32 9-point batch: the inner FP32 tolerance from a

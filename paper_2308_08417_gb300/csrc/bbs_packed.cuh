@@ -757,10 +757,12 @@ struct PackedGroup {
     bool valid;
     int sys;
     PackedOp<FMT, R> op;
-    __device__ __forceinline__ PackedGroup(const SolveParams& P, unsigned char* raw) {
+    // blk: the batch's block of 32 / L systems this warp solves (blockIdx.x
+    // unless the kernel strides over the batch)
+    __device__ __forceinline__ PackedGroup(const SolveParams& P, unsigned char* raw, int blk) {
         constexpr int S = 32 / L;
         const int lane = threadIdx.x & 31, g = lane / L;
-        const int s = blockIdx.x * S + g;
+        const int s = blk * S + g;
         valid = s < P.num_batch;
         sys = valid ? s : P.num_batch - 1;
         tm.tid = lane & (L - 1);
@@ -819,27 +821,41 @@ __device__ __forceinline__ bool packed_reject(const SolveParams& P, const Packed
 template <int FMT, int L, int R>
 __global__ void __launch_bounds__(32, packed_min_blocks(R)) bicgstab_packed_kernel(const SolveParams P) {
     extern __shared__ __align__(16) unsigned char raw[];
-    const PackedGroup<FMT, L, R> G(P, raw);
+    const PackedGroup<FMT, L, R> G(P, raw, blockIdx.x);
     if (packed_reject(P, G)) return;
     bicgstab_packed_system<FMT, L, R>(G.op, sys_io(P, G.sys), G.valid, solve_cfg(P, G.sys), G.sm, G.tm);
 }
 
 // GMRES: the group's small arrays follow its staged values in the slice.
+// The grid holds at most the blocks that stay resident at once, and each block
+// strides over the batch's blocks of systems; the Krylov basis of a group sits
+// in the workspace slot of its (block, group), so the whole basis store is
+// (resident blocks) x (32 / L) x (m + 1) x n_pad doubles and stays in L2
+// instead of being written to and re-read from DRAM for every system.
 template <int FMT, int L, int R>
 __global__ void __launch_bounds__(32, packed_cg_min_blocks(R)) gmres_packed_kernel(const SolveParams P) {
     extern __shared__ __align__(16) unsigned char raw[];
-    const PackedGroup<FMT, L, R> G(P, raw);
-    if (packed_reject(P, G)) return;
+    constexpr int S = 32 / L;
+    const int g = (threadIdx.x & 31) / L;
+    const int blocks = (P.num_batch + S - 1) / S;
     const size_t count = FMT == FMT_CSR ? (size_t)P.xk * P.n : P.vps;
-    unsigned char* slice = raw + (size_t)((threadIdx.x & 31) / L) * P.slice;
+    unsigned char* slice = raw + (size_t)g * P.slice;
     double* ext = reinterpret_cast<double*>(slice + P.stage_off + ((count * 8 + 15) & ~(size_t)15));
-    gmres_packed_system<FMT, L, R>(G.op, sys_io(P, G.sys), G.valid, solve_cfg(P, G.sys), G.sm.xa, ext, G.tm);
+    double* basis = P.ws + ((size_t)blockIdx.x * S + g) * (size_t)(P.restart + 1) * P.n_pad;
+    for (int blk = blockIdx.x; blk < blocks; blk += gridDim.x) {
+        const PackedGroup<FMT, L, R> G(P, raw, blk);
+        if (packed_reject(P, G)) return;
+        SolveCfg cfg = solve_cfg(P, G.sys);
+        cfg.ws = basis;
+        gmres_packed_system<FMT, L, R>(G.op, sys_io(P, G.sys), G.valid, cfg, G.sm.xa, ext, G.tm);
+        __syncwarp();  // the next block's staging overwrites the slices
+    }
 }
 
 template <int FMT, int L, int R>
 __global__ void __launch_bounds__(32, packed_cg_min_blocks(R)) cg_packed_kernel(const SolveParams P) {
     extern __shared__ __align__(16) unsigned char raw[];
-    const PackedGroup<FMT, L, R> G(P, raw);
+    const PackedGroup<FMT, L, R> G(P, raw, blockIdx.x);
     if (packed_reject(P, G)) return;
     cg_packed_system<FMT, L, R>(G.op, sys_io(P, G.sys), G.valid, solve_cfg(P, G.sys), G.sm, G.tm);
 }
