@@ -353,6 +353,8 @@ __global__ void gate_finalize_kernel(double* __restrict__ acc, double* __restric
 }  // namespace mlp
 }  // namespace bbs
 
+#include "bbs_mlp_infer.cuh"
+
 // ------------------------------------------------------------------ host
 
 using bbs::mlp::Epi;
@@ -387,6 +389,12 @@ struct bbs_mlp {
     size_t part_cap = 0;    // floats
     int sms = 0;
     int gemm_kind = BBS_GEMM_TCGEN05;  // or BBS_GEMM_MMA_SYNC
+    // fused inference (bbs_mlp_infer.cuh): TMA maps of the BF16 weights, the
+    // padded output width and the kernel's shared memory; fused = usable
+    CUtensorMap infer_maps[4];
+    int n_mma = 0;
+    size_t infer_smem = 0;
+    bool fused = false;
     std::vector<void*> allocs;
 };
 
@@ -662,6 +670,24 @@ bbs_status bbs_mlp_create(bbs_handle* h, int32_t n, int32_t hidden, uint64_t see
     const double gamma_one = 1.0;  // ungated until bbs_mlp_gate_finalize
     cudaMemcpy(m->gate, &gamma_one, sizeof(double), cudaMemcpyHostToDevice);
     pack_all(m, nullptr);
+    // fused inference (one kernel for the whole network) when its tiles fit:
+    // hidden and the 16-padded output width up to 256 (one MMA's N and the
+    // tensor-memory columns), the activation tile and weight ring in shared
+    // memory
+    m->n_mma = round_up(n, 16);
+    const bbs::mlp::InferSmem L = bbs::mlp::infer_smem(n, m->in_pad, hidden, m->n_mma);
+    m->infer_smem = L.total;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
+    m->fused = hidden <= 256 && m->n_mma <= 256 && L.total <= (size_t)optin;
+    for (int l = 0; l < 4 && m->fused; ++l)
+        m->fused = make_operand_map(&m->infer_maps[l], m->Wb[l], outs[l], m->pad_in[l], m->pad_in[l],
+                                    l < 3 ? hidden : m->n_mma);
+    if (m->fused)
+        m->fused = cudaFuncSetAttribute(bbs::mlp::mlp_infer_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)L.total) == cudaSuccess &&
+                   cudaFuncSetAttribute(bbs::mlp::mlp_infer_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)L.total) == cudaSuccess;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         bbs_mlp_destroy(m);
@@ -849,6 +875,48 @@ bbs_status bbs_mlp_forward(bbs_mlp* m, const uint16_t* feats, int32_t M, float* 
 
 }  // extern "C"
 
+// The tcgen05 path runs predictions and gate statistics through the fused
+// kernel when the network's tiles fit it.
+static bool uses_fused(const bbs_mlp* m) { return m->fused && m->gemm_kind == BBS_GEMM_TCGEN05; }
+
+// One launch of the fused network over the batch (128 systems per block):
+// x0 = x_prev + gamma * change (x_next == nullptr), or the gate statistics of
+// the change against x_next - x_prev.
+static bbs_status infer_fused(bbs_mlp* m, const bbs_batch_matrix* A, const double* b, const double* x_prev,
+                              const double* x_next, double* x0, cudaStream_t st) {
+    if (A->num_batch == 0) return BBS_OK;
+    bbs::mlp::InferParams p{};
+    p.num_batch = A->num_batch;
+    p.n = m->n;
+    p.nnz = A->nnz;
+    p.in_pad = m->in_pad;
+    p.hidden = m->hidden;
+    p.n_mma = m->n_mma;
+    p.row_ptrs = A->row_ptrs;
+    p.cols = A->col_idxs;
+    p.values = A->values;
+    p.b = b;
+    p.xp = x_prev;
+    p.xn = x_next;
+    p.x0 = x0;
+    p.acc = m->gate + 1;
+    for (int l = 0; l < 4; ++l) p.bias[l] = m->p + m->off_b[l];
+    p.mean = m->mean;
+    p.inv_std = m->inv_std;
+    p.stdv = m->stdv;
+    p.gamma = m->gate;
+    p.err = m->err;
+    const unsigned grid = (unsigned)((A->num_batch + bbs::mlp::kInferRows - 1) / bbs::mlp::kInferRows);
+    const auto& w = m->infer_maps;
+    if (x_next != nullptr)
+        bbs::mlp::mlp_infer_kernel<true><<<grid, bbs::mlp::kInferThreads, m->infer_smem, st>>>(w[0], w[1], w[2], w[3], p);
+    else
+        bbs::mlp::mlp_infer_kernel<false><<<grid, bbs::mlp::kInferThreads, m->infer_smem, st>>>(w[0], w[1], w[2], w[3],
+                                                                                              p);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BBS_OK : errf(BBS_ERR_CUDA, "%s", cudaGetErrorString(e));
+}
+
 // The network over a batch, max_batch rows at a time; `tail(r0, rows)`
 // consumes each piece's output in m->out.
 template <class Tail>
@@ -876,6 +944,7 @@ bbs_status bbs_mlp_predict(bbs_mlp* m, const bbs_batch_matrix* A, const double* 
     bbs_status s = check_csr_batch(m, A);
     if (s != BBS_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (uses_fused(m)) return infer_fused(m, A, b, x_prev, nullptr, x0, st);
     const int n = m->n;
     return run_batch(m, A, b, x_prev, st, [&](int r0, int rows) {
         bbs::mlp::predict_epilogue_kernel<<<std::min((rows * n + 255) / 256, 4096), 256, 0, st>>>(
@@ -889,6 +958,7 @@ bbs_status bbs_mlp_gate_observe(bbs_mlp* m, const bbs_batch_matrix* A, const dou
     bbs_status s = check_csr_batch(m, A);
     if (s != BBS_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (uses_fused(m)) return infer_fused(m, A, b, x_prev, x_next, nullptr, st);
     const int n = m->n;
     return run_batch(m, A, b, x_prev, st, [&](int r0, int rows) {
         bbs::mlp::gate_observe_kernel<<<std::min((rows * n + 255) / 256, 1024), 256, 0, st>>>(

@@ -105,6 +105,7 @@ def test_standardisation_and_predict(bbs):
     """Targets are standardised per component with the observed mean and
     standard deviation; predict returns x_prev + out * std + mean."""
     net = bbs.MLP(bbs.Handle(0), N, hidden=HID, seed=11, max_batch=1024)
+    net.set_gemm("mma")  # predict through the same layered GEMMs as forward()
     ts = W.time_stepped(num_batch=512, steps=4)
     dev = "cuda"
     A = bbs.DeviceBatch.from_batch(W.make_batch(ts.pattern, ts.values_at(1), "csr"), dev)
@@ -182,3 +183,62 @@ def test_gate_is_the_least_squares_scale(bbs):
         err_gated += float(((xn - x0) ** 2).sum())
         err_prev += float(((xn - xp) ** 2).sum())
     assert err_gated <= err_prev * (1 + 1e-12)
+
+
+def _fused_inputs(bbs, B, seed):
+    ts = W.time_stepped(num_batch=B, steps=3)
+    A = bbs.DeviceBatch.from_batch(W.make_batch(ts.pattern, ts.values_at(2), "csr"), "cuda")
+    b = torch.as_tensor(ts.rhs_at(2), device="cuda")
+    xp = torch.as_tensor(np.random.default_rng(seed).uniform(-1, 1, (B, N)), device="cuda")
+    return ts, A, b, xp
+
+
+def test_fused_predict_matches_oracle(bbs):
+    """The fused tcgen05 network (one kernel for all four layers, 128 systems
+    per block, a ragged last tile) against the FP64 oracle's forward pass with
+    BF16 rounding where the GPU stores BF16. Standardisation is the identity
+    before statistics are set, so x0 - x_prev is the network's output."""
+    net = bbs.MLP(bbs.Handle(0), N, hidden=HID, seed=3, max_batch=1024)
+    rng = np.random.default_rng(21)
+    params = OM.init_params(sizes(), rng)
+    net.set_params(torch.as_tensor(OM.flatten(params), dtype=torch.float32))
+    params = OM.unflatten(OM.flatten(params).astype(np.float32).astype(np.float64), sizes())
+    B = 300
+    ts, A, b, xp = _fused_inputs(bbs, B, 5)
+    x0 = net.predict(A, b, xp)
+    net.check()
+    got = (x0 - xp).cpu().numpy()
+    vals = ts.values_at(2)
+    rows = np.repeat(np.arange(N), np.diff(ts.pattern.row_ptrs))
+    diag = vals[:, np.nonzero(rows == ts.pattern.col_idxs)[0]]
+    X = np.concatenate([diag, ts.rhs_at(2), xp.cpu().numpy()], axis=1)
+    ref, _ = OM.forward(params, OM.to_bf16(X), round_bf16=True)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel < 1e-2, rel
+
+
+def test_fused_and_layered_paths_agree(bbs):
+    """The same network through the fused kernel (tcgen05) and through the
+    layered mma.sync GEMMs: predictions and gate statistics agree to BF16
+    accuracy."""
+    net = bbs.MLP(bbs.Handle(0), N, hidden=HID, seed=8, max_batch=2048)
+    B = 1000
+    ts, A, b, xp = _fused_inputs(bbs, B, 6)
+    noise = torch.as_tensor(np.random.default_rng(2).normal(scale=0.05, size=(B, N)), device="cuda")
+    net.observe(A, b, xp, xp + noise)
+    net.finalize_stats()
+    c = {}
+    for kind in ("tcgen05", "mma"):  # gamma = 1 until a gate is fitted
+        net.set_gemm(kind)
+        c[kind] = net.predict(A, b, xp) - xp
+    assert float(torch.linalg.norm(c["tcgen05"] - c["mma"]) / torch.linalg.norm(c["mma"])) < 1e-2
+    # a true change that is half the predicted one plus noise: gamma near 0.5
+    xn = xp + 0.5 * c["mma"] + 0.1 * torch.linalg.norm(c["mma"]) / np.sqrt(B * N) * noise / 0.05
+    g = {}
+    for kind in ("tcgen05", "mma"):
+        net.set_gemm(kind)
+        net.gate_observe(A, b, xp, xn)
+        net.gate_finalize()
+        g[kind] = net.gate()
+        net.check()
+    assert 0.3 < g["mma"] < 0.7 and abs(g["tcgen05"] - g["mma"]) < 2e-2 * g["mma"]
