@@ -13,7 +13,7 @@ with autotuned team sizes). The default line carries short measurements of
 these under "extras".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload scale|mixed|uneven|learned|pele|sweep|peaks]
+                  [--workload scale|mixed|uneven|learned|pele|sweep|peaks|mlp_predict]
                   [--systems N] [--shard] [--no-extras]
 
 --impl reference times the CPU oracle (plain C, OpenMP) on a bounded sample
@@ -102,7 +102,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="scale",
-                   choices=["scale", "mixed", "uneven", "learned", "pele", "sweep", "peaks"])
+                   choices=["scale", "mixed", "uneven", "learned", "pele", "sweep", "peaks", "mlp_predict"])
     p.add_argument("--format", default="csr", choices=["csr", "ell", "dense"],
                    help="batch format of the scale workload")
     p.add_argument("--solver", default="bicgstab", choices=["bicgstab", "cg", "gmres"],
@@ -559,6 +559,47 @@ def learned_run(bbs, torch, dev, eval_steps=192, num_batch=16384):
     return s
 
 
+def mlp_predict_run(bbs, torch, dev, stream, args, num_batch=16384, n=144, hidden=256):
+    """bbs_mlp_predict alone: the learned guess's network over one step of the
+    time-stepped batch (a network of the bench's shape, its initial weights;
+    the work does not depend on their values)."""
+    ts = W.time_stepped(num_batch=num_batch, steps=3)
+    A = bbs.DeviceBatch.from_batch(W.make_batch(ts.pattern, ts.values_at(2), "csr"), dev)
+    b = torch.as_tensor(ts.rhs_at(2), device=dev)
+    xp = torch.as_tensor(np.random.default_rng(1).uniform(-1, 1, (num_batch, n)), device=dev)
+    net = bbs.MLP(bbs.Handle(dev.index or 0), n, hidden=hidden, seed=1, max_batch=num_batch)
+    x0 = torch.empty_like(xp)
+    for _ in range(max(args.warmup, 3)):
+        net.predict(A, b, xp, x0)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.nvtx.range_push("bbs.timed")
+    with ClockSampler(dev.index or 0) as clk:
+        for e0, e1 in ev:
+            e0.record(stream)
+            net.predict(A, b, xp, x0)
+            e1.record(stream)
+        torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    net.check()
+    ms = [a.elapsed_time(z) for a, z in ev]
+    flop = 2.0 * num_batch * (3 * n * hidden + 2 * hidden * hidden + hidden * n)
+    achieved = flop / (statistics.mean(ms) / 1e3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops (burst)"
+    except (OSError, KeyError, ValueError):
+        peak, src = 1900.0, "profiling recipe fallback (1.9 PFLOP/s bf16 burst)"
+    return {"metric": "bbs_mlp_predict time per step", "value": statistics.mean(ms), "unit": "ms",
+            "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "dtype": "bf16+f32",
+            "data": "synthetic", "config": {"workload": f"timestepped_stencil2d5_12x12_B{num_batch}_predict",
+                                            "network": f"{3 * n}-{hidden}-{hidden}-{hidden}-{n}"},
+            "gpu_launches": args.steps, "clocks": clk.summary(),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "mlp_infer_kernel",
+                         "peak_source": src, "flop_per_launch": flop}}
+
+
 def time_steps(r, torch, stream, steps, warmup, dist=None, sample_clocks=False, dev_index=0):
     for _ in range(max(warmup, 3)):
         r.reset()
@@ -783,6 +824,11 @@ def main():
             print(json.dumps({"workload": "peaks", "unit": "TFLOP/s", **pk, "clocks": clk.summary(),
                               "nominal_fp64": FP64_FLOP_PER_CLK_SM * NUM_SMS * 2.07e9 / 1e12,
                               "nominal_fp32": FP32_FLOP_PER_CLK_SM * NUM_SMS * 2.07e9 / 1e12}), flush=True)
+        return
+    if args.workload == "mlp_predict":
+        line = mlp_predict_run(bbs, torch, dev, stream, args)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         return
     if args.workload in ("pele", "sweep"):
         res = pele_runs(bbs, torch, dev) if args.workload == "pele" else sweep_runs(bbs, torch, dev)
