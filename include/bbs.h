@@ -160,9 +160,8 @@ bbs_status bbs_destroy(bbs_handle *handle);
 /* Bytes of DEVICE workspace bbs_solve needs for this problem (0 is possible).
  * Workspace use: the FP32 copy of the values in mixed mode when values_f32
  * is NULL and the values are not staged in shared memory, the GMRES Krylov
- * basis ((restart + 1) * n_pad doubles per system when it does not fit in
- * shared memory; for packed systems per group of the resident grid, at most
- * SMs x resident blocks x 32 / lanes bases however large the batch), the
+ * basis ((restart + 1) * n_pad doubles per system; always for packed
+ * systems, else when it does not fit in shared memory), the
  * ILU(0) level schedule of the shared pattern, and for packed systems on CSR
  * the pattern as an ELL column table (2 * ell_k * n int32 + 256 bytes). */
 bbs_status bbs_workspace_size(const bbs_handle *handle, const bbs_batch_matrix *A,

@@ -93,7 +93,6 @@ struct Plan {
     size_t slice = 0;       // packed: shared-memory bytes per system
     size_t ws_gmres = 0, ws_f32 = 0, ws_ilu = 0;
     size_t ws_tables = 0;   // packed CSR: ELL column table, value map and flag
-    int grid = 0;           // blocks of the solver launch when not one per system (group)
 };
 
 bbs_status validate(const bbs_batch_matrix* A, const bbs_options* o) {
@@ -236,14 +235,9 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
                 p->ilu = true;
                 p->ws_ilu = align_up(bbs::ilu_workspace_bytes(n), 256);
             }
-            if (gmres) {  // the Krylov basis in the workspace, (m + 1) x n_pad per group of
-                          // the grid: at most the resident blocks, striding over the batch
-                const int S = 32 / L;
-                const long long blocks = ((long long)A->num_batch + S - 1) / S;
-                const long long resident = std::max(1LL, (long long)h->sms * packed_warps_per_sm(smem, R));
-                p->grid = (int)std::min(blocks, resident);
+            if (gmres) {  // the Krylov basis in the workspace, (m + 1) x n_pad per system
                 p->gmres_ws = true;
-                p->ws_gmres = (mr + 1) * (size_t)n_pad * 8 * (size_t)p->grid * (size_t)S;
+                p->ws_gmres = (mr + 1) * (size_t)n_pad * 8 * (size_t)A->num_batch;
             }
             return BBS_OK;
         }
@@ -502,7 +496,7 @@ bbs_status bbs_describe(const bbs_handle* h, const bbs_batch_matrix* A, const bb
         info->kernel = p.ilu ? "bicgstab_ilu_packed_kernel"
                        : o->solver == BBS_SOLVER_CG ? "cg_packed_kernel"
                        : o->solver == BBS_SOLVER_GMRES ? "gmres_packed_kernel" : "bicgstab_packed_kernel";
-        info->grid = p.grid > 0 ? p.grid : (A->num_batch + 32 / p.lanes - 1) / (32 / p.lanes);
+        info->grid = (A->num_batch + 32 / p.lanes - 1) / (32 / p.lanes);
         info->threads_per_system = p.lanes;
     } else {
         info->kernel = p.ilu ? "bicgstab_ilu_kernel"
@@ -641,7 +635,7 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
                                                          : bbs::bicgstab_packed_fn(A->fmt, p.lanes, p.R);
         if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         void* args[] = {&P, &csched};  // the ILU(0) kernels take the schedule as a second argument
-        const unsigned blocks = p.grid > 0 ? (unsigned)p.grid : (unsigned)((A->num_batch + per_block - 1) / per_block);
+        const unsigned blocks = (unsigned)((A->num_batch + per_block - 1) / per_block);
         e = cudaLaunchKernel(fn, dim3(blocks), dim3(32), args, p.smem, st);
         return e == cudaSuccess ? BBS_OK : cuda_fail(e, "packed solver launch");
     }

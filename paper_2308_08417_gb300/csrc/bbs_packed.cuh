@@ -827,29 +827,15 @@ __global__ void __launch_bounds__(32, packed_min_blocks(R)) bicgstab_packed_kern
 }
 
 // GMRES: the group's small arrays follow its staged values in the slice.
-// The grid holds at most the blocks that stay resident at once, and each block
-// strides over the batch's blocks of systems; the Krylov basis of a group sits
-// in the workspace slot of its (block, group), so the whole basis store is
-// (resident blocks) x (32 / L) x (m + 1) x n_pad doubles and stays in L2
-// instead of being written to and re-read from DRAM for every system.
 template <int FMT, int L, int R>
 __global__ void __launch_bounds__(32, packed_cg_min_blocks(R)) gmres_packed_kernel(const SolveParams P) {
     extern __shared__ __align__(16) unsigned char raw[];
-    constexpr int S = 32 / L;
-    const int g = (threadIdx.x & 31) / L;
-    const int blocks = (P.num_batch + S - 1) / S;
+    const PackedGroup<FMT, L, R> G(P, raw, blockIdx.x);
+    if (packed_reject(P, G)) return;
     const size_t count = FMT == FMT_CSR ? (size_t)P.xk * P.n : P.vps;
-    unsigned char* slice = raw + (size_t)g * P.slice;
+    unsigned char* slice = raw + (size_t)((threadIdx.x & 31) / L) * P.slice;
     double* ext = reinterpret_cast<double*>(slice + P.stage_off + ((count * 8 + 15) & ~(size_t)15));
-    double* basis = P.ws + ((size_t)blockIdx.x * S + g) * (size_t)(P.restart + 1) * P.n_pad;
-    for (int blk = blockIdx.x; blk < blocks; blk += gridDim.x) {
-        const PackedGroup<FMT, L, R> G(P, raw, blk);
-        if (packed_reject(P, G)) return;
-        SolveCfg cfg = solve_cfg(P, G.sys);
-        cfg.ws = basis;
-        gmres_packed_system<FMT, L, R>(G.op, sys_io(P, G.sys), G.valid, cfg, G.sm.xa, ext, G.tm);
-        __syncwarp();  // the next block's staging overwrites the slices
-    }
+    gmres_packed_system<FMT, L, R>(G.op, sys_io(P, G.sys), G.valid, solve_cfg(P, G.sys), G.sm.xa, ext, G.tm);
 }
 
 template <int FMT, int L, int R>

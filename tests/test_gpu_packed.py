@@ -352,28 +352,3 @@ def test_host_buffer_chunks_match_the_device_solve(bbs, handle):
     assert np.array_equal(hx.numpy(), dev[0])
     assert np.array_equal(log.iters.numpy(), dev[1]) and np.array_equal(log.status.numpy(), dev[3])
     assert np.array_equal(log.rel_res.numpy(), dev[2])
-
-
-def test_gmres_grid_stride_bitwise(bbs, handle):
-    """Packed GMRES runs on at most the resident blocks, each striding over
-    the batch with its basis in a per-(block, group) workspace slot: a batch
-    larger than one resident wave gives every system the bits of chunked
-    calls that each fit in one wave, and the workspace stops growing with the
-    batch."""
-    wl = W.plain_at_scale(12000)
-    A = wl.matrix("csr")
-    dA = bbs.DeviceBatch.from_batch(A, "cuda")
-    o = bbs.bbs_default_options(solver="gmres")
-    info = handle.describe(dA, o)
-    assert info["kernel"] == "gmres_packed_kernel"
-    assert info["grid"] < (12000 + 1) // 2  # the grid strides
-    small = bbs.DeviceBatch.from_batch(A.subset(np.arange(2000)), "cuda")
-    assert handle.workspace_size(dA, o) == handle.workspace_size(
-        bbs.DeviceBatch.from_batch(A.subset(np.arange(2 * info["grid"])), "cuda"), o)
-    whole = gpu_solve(bbs, handle, A, wl.b, solver="gmres")
-    for c0 in range(0, 12000, 2000):
-        part = gpu_solve(bbs, handle, A.subset(np.arange(c0, c0 + 2000)), wl.b[c0:c0 + 2000], solver="gmres")
-        for k in range(4):
-            assert np.array_equal(part[k], whole[k][c0:c0 + 2000])
-    assert handle.describe(small, o)["grid"] == 1000
-    assert (whole[3] == 0).all()
