@@ -2,7 +2,9 @@
 
 Bar (stated per system):
   * status codes equal exactly;
-  * iteration counts within +-2 (tree vs serial reductions change rounding);
+  * iteration counts within +-2 (tree vs serial reductions change rounding),
+    or, where a test says so, within +-2 plus the oracle's own spread when
+    the values are perturbed at rounding level (iteration_spread);
   * relative solution error <= 1e-8 for converged systems at tol 1e-10;
   * the logged relative residual of every converged system is <= tol and
     matches the residual of the returned x recomputed on the host in long
@@ -32,9 +34,11 @@ def compare(x_gpu, it_gpu, rel_gpu, st_gpu, x_ref, it_ref, st_ref, *, tol=1e-10,
         bad = np.nonzero(st_gpu != st_ref)[0][:8]
         fails.append(f"{label} status differs at {bad}: gpu {st_gpu[bad]} oracle {st_ref[bad]}")
     d = np.abs(it_gpu.astype(np.int64) - it_ref.astype(np.int64))
-    if d.max(initial=0) > iter_tol:
-        i = int(np.argmax(d))
-        fails.append(f"{label} iterations differ by {d.max()} (system {i}: gpu {it_gpu[i]} oracle {it_ref[i]})")
+    over = d - np.broadcast_to(np.asarray(iter_tol, dtype=np.int64), d.shape)
+    if over.max(initial=0) > 0:
+        i = int(np.argmax(over))
+        fails.append(f"{label} iterations differ by {d[i]} (system {i}: gpu {it_gpu[i]} oracle {it_ref[i]}, "
+                     f"allowed {np.broadcast_to(iter_tol, d.shape)[i]})")
     conv = (st_ref == 0) & (st_gpu == 0)
     if conv.any():
         e = np.linalg.norm(x_gpu[conv] - x_ref[conv], axis=1) / np.maximum(
@@ -51,3 +55,17 @@ def compare(x_gpu, it_gpu, rel_gpu, st_gpu, x_ref, it_ref, st_ref, *, tol=1e-10,
             if (rh > tol * (1 + 1e-6)).any():
                 fails.append(f"{label} host-recomputed residual above tol: {rh.max():.3e}")
     return fails
+
+
+def iteration_spread(solve, A, b, *args, seeds=range(1, 9), rel=1e-15, **kw):
+    """Per system, the range of the oracle's own iteration counts when the
+    matrix values are perturbed by `rel` relative (eight seeds): how far
+    rounding alone moves that system's count."""
+    its = []
+    for s in seeds:
+        rng = np.random.default_rng(s)
+        Ap = A.subset(np.arange(A.num_batch))
+        Ap.values = A.values * (1.0 + rel * rng.uniform(-1.0, 1.0, A.values.shape))
+        its.append(np.asarray(solve(Ap, b, *args, **kw)[1], dtype=np.int64))
+    its = np.array(its)
+    return its.max(axis=0) - its.min(axis=0)

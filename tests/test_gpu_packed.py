@@ -13,7 +13,7 @@ import torch
 
 import oracle
 from paper_2308_08417_gb300 import workloads as W
-from tests.parity import compare, host_rel_residual
+from tests.parity import compare, host_rel_residual, iteration_spread
 from tests.test_gpu_parity import dense_of, gpu_solve
 
 pytestmark = pytest.mark.gpu
@@ -68,12 +68,14 @@ def test_formats_and_preconditioners(bbs, handle, fmt, precond):
     for L in (0, 16):
         g = gpu_solve(bbs, handle, A, wl.b, threads_per_system=L, precond=precond, max_iters=2000)
         r = oracle.solve_batch(A, wl.b, precond=precond, max_iters=2000)
-        # Without preconditioning the iteration count of this batch is
-        # sensitive to rounding: the oracle itself takes 26 to 30 iterations on
-        # one system when its values are perturbed by 1e-15 relative. The
-        # solutions and residuals keep the full bar.
+        # Without preconditioning some iteration counts of this batch are
+        # sensitive to rounding (the oracle itself moves by up to 4 iterations
+        # on one system when the values are perturbed by 1e-15 relative): each
+        # system gets +-2 plus its own spread. Solutions and residuals keep
+        # the full bar.
+        spread = iteration_spread(oracle.solve_batch, A, wl.b, precond=precond, max_iters=2000)
         fails = compare(*g[:4], r[0], r[1], r[3], rel_host=host_rel_residual(dense_of(wl), g[0], wl.b),
-                        iter_tol=2 if precond == "jacobi" else 5, label=f"{fmt}/{precond}/L={L}")
+                        iter_tol=2 + spread, label=f"{fmt}/{precond}/L={L}")
         assert not fails, "\n".join(fails)
 
 
@@ -214,8 +216,10 @@ def test_gmres_default_and_edges(bbs, handle):
         r = oracle.solve_batch(A2, b, x0, solver="gmres", precond=precond)
         assert g[3][5] == 3 and g[3][9] == 3 and g[3][3] == 0 and g[1][3] == 0 and (g[0][3] == 0).all()
         keep = np.setdiff1d(np.arange(301), [5, 9])
+        spread = iteration_spread(oracle.solve_batch, A2.subset(keep), b[keep], x0[keep], solver="gmres",
+                                  precond=precond)
         fails = compare(g[0][keep], g[1][keep], g[2][keep], g[3][keep], r[0][keep], r[1][keep], r[3][keep],
-                        iter_tol=2 if precond == "jacobi" else 5, label=f"gmres edges {precond}")
+                        iter_tol=2 + spread, label=f"gmres edges {precond}")
         assert not fails, "\n".join(fails)
     g0 = gpu_solve(bbs, handle, A, wl.b, x0, solver="gmres", max_iters=0)
     assert (g0[1] == 0).all() and (g0[3] == 1).all() and np.array_equal(g0[0], x0)
