@@ -113,6 +113,8 @@ def parse():
                    help="launch shape of the scale and mixed workloads (0: the library's choice)")
     p.add_argument("--systems", type=int, default=0,
                    help="solve only the first N systems of the workload (profiling runs)")
+    p.add_argument("--inner-tol", type=float, default=0.0,
+                   help="mixed workload: inner FP32 tolerance (0: the tuned default)")
     p.add_argument("--shard", action="store_true",
                    help="ranks split one batch (strong scaling) instead of each solving a full batch")
     p.add_argument("--no-e2e", action="store_true")
@@ -398,11 +400,12 @@ class Uneven:
 
 
 def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0, solver="bicgstab",
-                precond="jacobi", span=None):
+                precond="jacobi", span=None, inner_tol=0.0):
     if name == "mixed":
         wl = span_workload(subset_workload(W.mixed_precision(), systems), span)
-        # inner tolerance 1e-2: the fastest of 0.3 / 0.1 / 0.03 / 1e-2 / 1e-3 / 1e-4 in a sweep
         kw = dict(MIXED_OPTS)
+        if inner_tol:
+            kw["inner_tol"] = inner_tol
         if tps:
             kw["threads_per_system"] = tps
         return Uniform(bbs, torch, dev, wl, "ell", kw, wl.name)
@@ -850,7 +853,8 @@ def main():
         return
     span = shard_span(args.workload, args.systems, rank, world) if args.shard else None
     r = make_runner(args.workload, bbs, torch, dev, args.systems, tune=not args.no_tune, fmt=args.format,
-                    tps=args.threads_per_system, solver=args.solver, precond=args.precond, span=span)
+                    tps=args.threads_per_system, solver=args.solver, precond=args.precond, span=span,
+                    inner_tol=args.inner_tol)
     total_ms, solve_ms, clocks = time_steps(r, torch, stream, args.steps, args.warmup, dist,
                                             sample_clocks=True, dev_index=local)
     total_ms = max_over_ranks(total_ms, dist, dev)  # the job's time is its slowest rank's
