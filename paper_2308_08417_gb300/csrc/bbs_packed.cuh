@@ -704,6 +704,17 @@ __device__ __forceinline__ void gmres_packed_system(const PackedOp<FMT, R>& op, 
         const double res = packed_residual<FMT, L, R>(op, io.b, xs, r, false, xa, tm, n);
         if (nan_exit) res2 = res;
     }
+    // The basis is dead scratch from here on: drop the 128-byte lines wholly
+    // inside this system's slot from L2 without writing them back (dirty lines
+    // of finished systems would otherwise crowd live data out of L2 and be
+    // written to DRAM when evicted).
+    __syncwarp();
+    if (valid && V != nullptr) {
+        const uintptr_t first = (reinterpret_cast<uintptr_t>(V) + 127) & ~static_cast<uintptr_t>(127);
+        const uintptr_t end = (reinterpret_cast<uintptr_t>(V) + (size_t)(m + 1) * vs * 8) & ~static_cast<uintptr_t>(127);
+        for (uintptr_t a = first + (uintptr_t)tm.tid * 128; a < end; a += (uintptr_t)L * 128)
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+    }
     if (!valid) return;
     if (special == 1) {
         if (tm.tid == 0) {

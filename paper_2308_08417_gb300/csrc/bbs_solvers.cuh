@@ -799,6 +799,15 @@ __device__ __forceinline__ void gmres_system(const Op<FMT, R, double, double>& o
     }
     double res2 = beta2;
     if (status == ST_NAN) res2 = true_residual(op, b, x, r, sm.xa, sm.red, parity, tm, n);
+    if (C.ws != nullptr) {  // a basis in the workspace is dead scratch now: drop its
+                            // whole 128-byte lines from L2 without a write-back
+        tm.sync();
+        const uintptr_t first = (reinterpret_cast<uintptr_t>(V) + 127) & ~static_cast<uintptr_t>(127);
+        const uintptr_t end =
+            (reinterpret_cast<uintptr_t>(V) + (size_t)(m + 1) * vstride * 8) & ~static_cast<uintptr_t>(127);
+        for (uintptr_t a = first + (uintptr_t)tm.tid * 128; a < end; a += (uintptr_t)tm.nt * 128)
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+    }
     write_result(io, x, status, it, sqrt(res2 / nb2), 0, tm);
 }
 
