@@ -284,11 +284,11 @@ bbs_status make_plan(const bbs_handle* h, const bbs_batch_matrix* A, const bbs_o
         p->ws_ilu = align_up(bbs::ilu_workspace_bytes(n), 256);
         return BBS_OK;
     }
-    // mixed mode on ELL stages (FP32 value, column) pairs for every row slot
-    // of the block, R * ell_k * threads of them (the refinement kernel's
+    // mixed mode on ELL stages an FP32 value and a 16-bit column for every row
+    // slot of the block, R * ell_k * threads of each (the refinement kernel's
     // PairOp32); otherwise the values in their own layout
     const size_t stage_bytes = (mixed && A->fmt == BBS_FMT_ELL)
-                                   ? align_up((size_t)p->R * (size_t)A->ell_k * (size_t)p->threads * 8, 16)
+                                   ? align_up((size_t)p->R * (size_t)A->ell_k * (size_t)p->threads * 6, 16)
                                    : align_up(vps * (mixed ? 4 : 8), 16);
     const size_t limit = (size_t)h->max_smem_optin;
     bool stage = false;
@@ -312,10 +312,11 @@ size_t workspace_bytes(const Plan& p) {
 
 // BiCGSTAB with staged values and Jacobi runs the Jacobi-folded kernel; the
 // mixed mode on ELL with staged values takes an instance for its ELL width
-// when there is one.
-const void* pick_kernel(const bbs_options* o, int fmt, int R, bool staged, int ell_k) {
+// when there is one and the block has at most 256 threads (those instances
+// are compiled for three resident blocks).
+const void* pick_kernel(const bbs_options* o, int fmt, int R, bool staged, int ell_k, int threads) {
     if (o->precision == BBS_PRECISION_MIXED_IR) {
-        const void* fn = (fmt == BBS_FMT_ELL && staged) ? bbs::refine_ell_fn(R, ell_k) : nullptr;
+        const void* fn = (fmt == BBS_FMT_ELL && staged && threads <= 256) ? bbs::refine_ell_fn(R, ell_k) : nullptr;
         return fn != nullptr ? fn : bbs::refine_fn(fmt, R);
     }
     switch (o->solver) {
@@ -639,7 +640,7 @@ bbs_status bbs_solve(bbs_handle* h, const bbs_batch_matrix* A, const double* b, 
         e = cudaLaunchKernel(fn, dim3(blocks), dim3(32), args, p.smem, st);
         return e == cudaSuccess ? BBS_OK : cuda_fail(e, "packed solver launch");
     }
-    const void* fn = pick_kernel(o, A->fmt, p.R, p.stage, A->ell_k);
+    const void* fn = pick_kernel(o, A->fmt, p.R, p.stage, A->ell_k, p.threads);
     if ((e = allow_smem(fn, p.smem)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     void* args[] = {&P};
     e = cudaLaunchKernel(fn, dim3((unsigned)A->num_batch), dim3((unsigned)p.threads), args, p.smem, st);

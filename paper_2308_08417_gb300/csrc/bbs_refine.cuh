@@ -106,17 +106,19 @@ __device__ __forceinline__ void stage_values_rounded(const double* __restrict__ 
     for (size_t j = i + tm.tid; j < count; j += tm.nt) s[j] = (float)ldg(g + j);
 }
 
-// Staged FP32 ELL values as (value, column) pairs in each thread's own
-// order: pair (q k + j) nt + t holds slot j of row t + q nt, so one 8-byte
-// shared-memory load gives a slot's value and column and consecutive threads
-// read consecutive pairs. Padding slots and rows past n carry value 0 and
-// column n, a zero kept after the end of every FP32 SpMV input vector, so the
-// SpMV has no branch. The values are the FP32 copy's, or the FP64 values
-// rounded to nearest as they are staged.
+// Staged FP32 ELL values in each thread's own order: slot j of row t + q nt
+// is entry (q k + j) nt + t of an FP32 value array and of a 16-bit column
+// array after it (6 bytes a slot, so that three 256-thread blocks of the
+// n = 1,024 batch fit in an SM's shared memory), and consecutive threads read
+// consecutive entries. Padding slots and rows past n carry value 0 and column
+// n, a zero kept after the end of every FP32 SpMV input vector, so the SpMV
+// has no branch. The values are the FP32 copy's, or the FP64 values rounded
+// to nearest as they are staged.
 template <int R>
 __device__ __forceinline__ void stage_pairs_ell(const double* __restrict__ g64, const float* __restrict__ g32,
-                                                const int32_t* __restrict__ cols, float2* __restrict__ pairs,
+                                                const int32_t* __restrict__ cols, float* __restrict__ vals,
                                                 int n, int k, const Team& tm) {
+    uint16_t* cl = reinterpret_cast<uint16_t*>(vals + (size_t)R * k * tm.nt);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int row = tm.row(q);
@@ -131,24 +133,28 @@ __device__ __forceinline__ void stage_pairs_ell(const double* __restrict__ g64, 
                     v = g32 != nullptr ? ldg(g32 + i) : (float)ldg(g64 + i);
                 }
             }
-            pairs[(size_t)(q * k + j) * tm.nt + tm.tid] = make_float2(v, __int_as_float(c));
+            const size_t o = (size_t)(q * k + j) * tm.nt + tm.tid;
+            vals[o] = v;
+            cl[o] = (uint16_t)c;
         }
     }
 }
 
-// y = A x over the staged pairs (slots in ascending column order, FMA).
-// K > 0 fixes the ELL width at compile time (the multi-level dispatch of
-// Sec. 3.3 applied to the stencil width): the slot loop then unrolls fully,
-// every pair sits at a constant multiple of the thread stride, and the R
-// rows' FMA chains interleave. K = 0 takes the width k at run time.
+// y = A x over the staged values and columns (slots in ascending column
+// order, FMA). K > 0 fixes the ELL width at compile time (the multi-level
+// dispatch of Sec. 3.3 applied to the stencil width): the slot loop then
+// unrolls fully, every entry sits at a constant multiple of the thread
+// stride, and the R rows' FMA chains interleave. K = 0 takes the width k at
+// run time.
 template <int R, int K = 0>
 struct PairOp32 {
-    const float2* __restrict__ pairs;
+    const float* __restrict__ vals;
     int k;
     __device__ __forceinline__ void apply(const float* __restrict__ xs, float (&y)[R], const Team& tm) const {
-        const float2* p = pairs + tm.tid;
+        const int kk = K > 0 ? K : k;
+        const uint16_t* cl = reinterpret_cast<const uint16_t*>(vals + (size_t)R * kk * tm.nt);
+        const int nt = tm.nt;
         if constexpr (K > 0) {
-            const int nt = tm.nt;
             float sum[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) sum[q] = 0.0f;
@@ -156,8 +162,8 @@ struct PairOp32 {
             for (int j = 0; j < K; ++j) {
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    const float2 e = p[(q * K + j) * nt];
-                    sum[q] = fmaf(e.x, xs[__float_as_int(e.y)], sum[q]);
+                    const int o = (q * K + j) * nt + tm.tid;
+                    sum[q] = fmaf(vals[o], xs[cl[o]], sum[q]);
                 }
             }
 #pragma unroll
@@ -166,11 +172,9 @@ struct PairOp32 {
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 float sum = 0.0f;
-#pragma unroll 3
-                for (int j = 0; j < k; ++j) {
-                    const float2 e = *p;
-                    p += tm.nt;
-                    sum = fmaf(e.x, xs[__float_as_int(e.y)], sum);
+                for (int j = 0; j < kk; ++j) {
+                    const int o = (q * kk + j) * nt + tm.tid;
+                    sum = fmaf(vals[o], xs[cl[o]], sum);
                 }
                 y[q] = sum;
             }
@@ -224,11 +228,14 @@ __device__ __forceinline__ void refine_system(const SolveParams& P, const SysIO&
 }
 
 // Shared memory: red64[256] | xd[n_pad] (FP64) | red32[256] | xa[n_pad + 2] |
-// xb[n_pad + 2] (FP32; entry n stays 0) | staged FP32 values or ELL pairs
-// (optional). K > 0 (ELL with staged values only): the pair SpMV for an ELL
-// width of exactly K.
+// xb[n_pad + 2] (FP32; entry n stays 0) | staged FP32 values (optional; on
+// ELL values and 16-bit columns, 6 bytes a slot). K > 0 (ELL with staged
+// values, at most 256 threads): the SpMV for an ELL width of exactly K, and
+// three resident blocks per SM (80 registers), which hide more of the inner
+// iteration's reduction and barrier latency than two.
 template <int FMT, int R, int K = 0>
-__global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const SolveParams P) {
+__global__ void __launch_bounds__(K > 0 ? 256 : max_threads_for(R), K > 0 ? 3 : 1)
+    refine_kernel(const SolveParams P) {
     extern __shared__ __align__(16) unsigned char raw[];
     const Team tm = Team::block();
     const int sys = blockIdx.x;
@@ -257,10 +264,10 @@ __global__ void __launch_bounds__(max_threads_for(R), 1) refine_kernel(const Sol
     }
     if constexpr (FMT == FMT_ELL) {
         if (P.stage) {
-            float2* pairs = reinterpret_cast<float2*>(raw + P.stage_off);
-            stage_pairs_ell<R>(A64.vals, A32.vals, P.cols, pairs, n, P.k, tm);
+            float* vals = reinterpret_cast<float*>(raw + P.stage_off);
+            stage_pairs_ell<R>(A64.vals, A32.vals, P.cols, vals, n, P.k, tm);
             tm.sync();
-            const PairOp32<R, K> op32{pairs, P.k};
+            const PairOp32<R, K> op32{vals, P.k};
             refine_system<FMT, R>(P, io, op64, op32, dinv, red64, xd, red32, xa, xb, tm);
             return;
         }
