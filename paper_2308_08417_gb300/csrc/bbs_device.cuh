@@ -354,6 +354,61 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* red, int& parity, const
     }
 }
 
+// FP32 block sums of 5..8 values, identical bits on every thread. Blocks of
+// up to 16 warps use one barrier (two 16-byte slots per warp in the same
+// 128-float buffer); larger blocks reduce the first four values and the rest
+// in two rounds.
+template <int NV>
+__device__ __forceinline__ void block_sum_wide(float (&v)[NV], float* red, int& parity, const Team& tm) {
+    static_assert(NV > 4 && NV <= 8, "block_sum_wide handles 5..8 values");
+    float a[4] = {v[0], v[1], v[2], v[3]};
+    float c[NV - 4];
+#pragma unroll
+    for (int j = 0; j < NV - 4; ++j) c[j] = v[4 + j];
+    if (tm.nwarps > 16) {
+        block_sum(a, red, parity, tm);
+        block_sum(c, red, parity, tm);
+    } else {
+        warp_sum<float, 4>(a, tm.lane);
+        warp_sum<float, NV - 4>(c, tm.lane);
+        if (tm.nwarps > 1) {
+            float4* b4 = reinterpret_cast<float4*>(red + parity * 128);
+            parity ^= 1;
+            if (tm.lane == 0) {
+                float e[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int j = 0; j < NV - 4; ++j) e[j] = c[j];
+                b4[2 * tm.warp] = make_float4(a[0], a[1], a[2], a[3]);
+                b4[2 * tm.warp + 1] = make_float4(e[0], e[1], e[2], e[3]);
+            }
+            tm.sync();
+            float4 s = b4[0], u = b4[1];
+            for (int w = 1; w < tm.nwarps; ++w) {
+                const float4 p = b4[2 * w], q = b4[2 * w + 1];
+                s.x += p.x;
+                s.y += p.y;
+                s.z += p.z;
+                s.w += p.w;
+                u.x += q.x;
+                u.y += q.y;
+                u.z += q.z;
+                u.w += q.w;
+            }
+            a[0] = s.x;
+            a[1] = s.y;
+            a[2] = s.z;
+            a[3] = s.w;
+            const float uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int j = 0; j < NV - 4; ++j) c[j] = uu[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = a[j];
+#pragma unroll
+    for (int j = 0; j < NV - 4; ++j) v[4 + j] = c[j];
+}
+
 // Partial dot products over the caller's rows (rows beyond n hold zeros).
 template <int R, typename T>
 __device__ __forceinline__ T pdot(const T (&a)[R], const T (&b)[R]) {

@@ -14,7 +14,10 @@ namespace bbs {
 
 // FP32 BiCGSTAB from d = 0 on A32 d = w; stops when the recursive residual
 // passes inner_tol*||w||, on a breakdown or non-finite scalar, or after
-// max_inner iterations. Returns the iteration at which it stopped.
+// max_inner iterations. Returns the iteration at which it stopped. Two block
+// reductions per iteration instead of three: the norm of the new residual
+// and the next rho come from the dot products of s and t (the inner solve
+// only needs to shrink the residual; the FP64 outer loop judges the result).
 template <int R, class Op32>
 __device__ __forceinline__ int inner_bicgstab32(const Op32& op,
                                                 const float (&dinv)[R], const float (&w)[R],
@@ -62,8 +65,11 @@ __device__ __forceinline__ int inner_bicgstab32(const Op32& op,
         }
         tm.sync();
         op.apply(xb, t, tm);
-        float s3[3] = {pdot(r, r), pdot(t, t), pdot(t, r)};
-        block_sum(s3, red, parity, tm);
+        // One reduction closes the step. With r = s - omega t (s held in r):
+        // (r, r) = (s, s) - omega (2 (t, s) - omega (t, t)) and
+        // (rh, r) = (rh, s) - omega (rh, t), exact in exact arithmetic.
+        float s3[5] = {pdot(r, r), pdot(t, t), pdot(t, r), pdot(rh, r), pdot(rh, t)};
+        block_sum_wide(s3, red, parity, tm);
         if (s3[0] <= tau2) {
 #pragma unroll
             for (int q = 0; q < R; ++q) {
@@ -79,11 +85,10 @@ __device__ __forceinline__ int inner_bicgstab32(const Op32& op,
             if (row < n) d[q] = fmaf(omega, xb[row], fmaf(alpha, xa[row], d[q]));
             r[q] = fmaf(-omega, t[q], r[q]);
         }
-        float s2[2] = {pdot(r, r), pdot(rh, r)};
-        block_sum(s2, red, parity, tm);
-        if (!finite(s2[0]) || s2[0] <= tau2 || omega == 0.0f) return it;
+        const float rr = fmaf(-omega, fmaf(-omega, s3[1], 2.0f * s3[2]), s3[0]);
+        if (!finite(rr) || rr <= tau2 || omega == 0.0f) return it;
         rho_old = rho;
-        rho = s2[1];
+        rho = fmaf(-omega, s3[4], s3[3]);
     }
     return max_inner;
 }
