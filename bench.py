@@ -337,10 +337,15 @@ class Uneven:
                        if tune else None)
         self.tune_s = time.perf_counter() - t0
         self.plan = bbs.VarPlan(self.h, self.vbd, self.opts, self.tuning)
+        self.desc = self.plan.describe()
         self.log = bbs.Log.empty(vb.num_batch, device=dev)
         self.num_batch = vb.num_batch
-        self.kernel = "varsize_kernel"
-        self.launches_per_step = 1
+        # one graph: the persistent team launch (with its counter reset) and
+        # one launch per packed class of small systems
+        persistent = 1 if self.desc["persistent_grid"] else 0
+        self.kernel = ("varsize_kernel" if not self.desc["packed_launches"]
+                       else "varsize_kernel+varpacked_kernel" if persistent else "varpacked_kernel")
+        self.launches_per_step = persistent + self.desc["packed_launches"]
         self.mixed = False
 
     def reset(self):
@@ -362,7 +367,7 @@ class Uneven:
         st = self.log.status.cpu().numpy()
         return {"mean": float(it.mean()), "max": int(it.max()), "converged": int((st == 0).sum()),
                 "tuning": self.tuning.as_dict() if self.tuning is not None else "default",
-                "tune_s": self.tune_s}
+                "tune_s": self.tune_s, "plan": self.desc}
 
     def e2e(self, reps):
         torch = self.torch
@@ -744,7 +749,8 @@ def extras(bbs, torch, dev, stream, mhz, peaks=None):
         tot, ms, _ = time_steps(un, torch, stream, 5, 2)
         out["uneven"] = {"workload": un.label, "value": un.num_batch * 5 / (tot / 1e3),
                          "unit": "systems/s", "iterations": un.summary(),
-                         "roofline": roofline(un, ms, mhz, peaks), "launches_per_step": "1 graph (memset + kernel)"}
+                         "roofline": roofline(un, ms, mhz, peaks),
+                         "launches_per_step": f"1 graph ({un.launches_per_step} kernels)"}
         del un
     except Exception as e:
         out["uneven"] = {"error": repr(e)}

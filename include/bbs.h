@@ -303,15 +303,20 @@ typedef struct {
 /* Launch choices for an uneven batch. Systems fall in size buckets
  * (bucket b holds n <= bucket_max_n[b], ascending); each bucket has the number
  * of warps that solve one of its systems (1, 2, 4, 8 or 16; at most
- * block_warps) and whether its systems' values are staged in shared memory.
- * block_warps is 8 (up to 8 rows per thread) or 16 (up to 4 rows per thread).
- * The planner lowers a bucket's warps to those of the next larger bucket if
- * they exceed them and raises them to the minimum its rows need. */
+ * block_warps), whether its systems' values are staged in shared memory, and
+ * whether its small systems are packed (pack[b] = 1: a system of at most 160
+ * rows whose group fits shared memory is solved by 4, 8 or 16 lanes, with
+ * 8, 4 or 2 systems per warp in lockstep, as bbs_solve packs uniform batches;
+ * 0: one team per system). block_warps is 8 (up to 8 rows per thread) or 16
+ * (up to 4 rows per thread). The planner lowers a bucket's warps to those of
+ * the next larger bucket if they exceed them and raises them to the minimum
+ * its rows need. */
 typedef struct {
     int32_t num_buckets; /* 1..8 */
     int32_t bucket_max_n[8];
     int32_t team_warps[8];
     int32_t stage_values[8];
+    int32_t pack[8];
     int32_t block_warps;
     int32_t reserved;
 } bbs_var_tuning;
@@ -319,14 +324,22 @@ typedef struct {
 typedef struct bbs_var_plan bbs_var_plan;
 
 /* Default tuning: power-of-two buckets up to max_n, one warp per 5 rows per
- * thread (as bbs_default_block_size), values streamed, 8-warp blocks. Host only. */
+ * thread (as bbs_default_block_size), values streamed, small systems packed,
+ * 8-warp blocks. Host only. */
 bbs_status bbs_var_default_tuning(int32_t max_n, bbs_var_tuning *tuning);
 
 /* Plan the persistent solve of `batch` (FP64, BiCGSTAB or CG, Jacobi or
- * none): order the systems longest first, group them in segments of equal
- * team size, size the grid to fill every SM and capture "reset the work
- * counters + one persistent launch" in a CUDA graph. Allocates the plan's own
- * device buffers (system order, counters). tuning NULL = default tuning. */
+ * none). The systems that run packed (see bbs_var_tuning.pack) are grouped by
+ * (lanes per system, rows per lane), one launch per group; the planner reads
+ * their patterns' row pointers (rejecting, with BBS_ERR_INVALID_ARG, row
+ * pointers that do not ascend within [0, nnz]) and builds an ELL column table
+ * of each such pattern on the device. The other systems are ordered longest
+ * first and grouped in segments of equal team size for one persistent launch
+ * whose grid fills every SM. The CUDA graph holds "reset the work counters ->
+ * the persistent launch" and, beside it, the packed launches. Allocates the
+ * plan's own device buffers (system order, counters, tables). The patterns
+ * must not change while the plan lives (values, b and x may). tuning NULL =
+ * default tuning. */
 bbs_status bbs_var_plan_create(bbs_handle *handle, const bbs_var_batch *batch,
                                const bbs_var_host_info *host, const bbs_options *opts,
                                const bbs_var_tuning *tuning, bbs_var_plan **plan);
@@ -336,6 +349,18 @@ bbs_status bbs_var_plan_create(bbs_handle *handle, const bbs_var_batch *batch,
  * Asynchronous. Plans of the same handle must not run concurrently. */
 bbs_status bbs_var_solve(bbs_var_plan *plan, const double *b, double *x, const bbs_log *log,
                          void *stream);
+
+/* What a plan runs: systems solved by teams in the persistent launch, systems
+ * solved packed and the number of packed launches, and the persistent grid
+ * (0 when every system is packed). Host only. */
+typedef struct {
+    int32_t team_systems;
+    int32_t packed_systems;
+    int32_t packed_launches;
+    int32_t persistent_grid;
+} bbs_var_plan_desc;
+
+bbs_status bbs_var_plan_describe(const bbs_var_plan *plan, bbs_var_plan_desc *desc);
 
 /* Release a plan (waits for its graph to finish). NULL is accepted. */
 bbs_status bbs_var_plan_destroy(bbs_var_plan *plan);

@@ -63,15 +63,21 @@ class bbs_var_host_info(C.Structure):
     _fields_ = [("pat_n", C.c_void_p), ("pat_nnz", C.c_void_p), ("sys_pattern", C.c_void_p)]
 
 
+class bbs_var_plan_desc(C.Structure):
+    _fields_ = [("team_systems", C.c_int32), ("packed_systems", C.c_int32),
+                ("packed_launches", C.c_int32), ("persistent_grid", C.c_int32)]
+
+
 class bbs_var_tuning(C.Structure):
     _fields_ = [("num_buckets", C.c_int32), ("bucket_max_n", C.c_int32 * 8),
                 ("team_warps", C.c_int32 * 8), ("stage_values", C.c_int32 * 8),
-                ("block_warps", C.c_int32), ("reserved", C.c_int32)]
+                ("pack", C.c_int32 * 8), ("block_warps", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self) -> dict:
         k = self.num_buckets
         return {"bucket_max_n": list(self.bucket_max_n[:k]), "team_warps": list(self.team_warps[:k]),
-                "stage_values": list(self.stage_values[:k]), "block_warps": self.block_warps}
+                "stage_values": list(self.stage_values[:k]), "pack": list(self.pack[:k]),
+                "block_warps": self.block_warps}
 
     @classmethod
     def from_dict(cls, d: dict) -> "bbs_var_tuning":
@@ -82,6 +88,7 @@ class bbs_var_tuning(C.Structure):
             t.bucket_max_n[i] = d["bucket_max_n"][i]
             t.team_warps[i] = d["team_warps"][i]
             t.stage_values[i] = d["stage_values"][i]
+            t.pack[i] = d.get("pack", [1] * k)[i]
         t.block_warps = d["block_warps"]
         return t
 
@@ -116,6 +123,7 @@ def lib():
                                           P(bbs_options), P(bbs_var_tuning), P(C.c_void_p)]
         L.bbs_var_solve.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, P(bbs_log), C.c_void_p]
         L.bbs_var_plan_destroy.argtypes = [C.c_void_p]
+        L.bbs_var_plan_describe.argtypes = [C.c_void_p, P(bbs_var_plan_desc)]
         L.bbs_var_tune.argtypes = [C.c_void_p, P(bbs_var_batch), P(bbs_var_host_info), C.c_void_p,
                                    C.c_void_p, P(bbs_options), C.c_int32, P(bbs_var_tuning)]
         vp, i32, st = C.c_void_p, C.c_int32, C.c_void_p
@@ -150,6 +158,7 @@ def lib():
         for name in ("bbs_default_options", "bbs_create", "bbs_destroy", "bbs_workspace_size", "bbs_describe", "bbs_check_pattern",
                      "bbs_solve", "bbs_solve_host", "bbs_solve_noalloc", "bbs_var_default_tuning",
                      "bbs_var_plan_create", "bbs_var_solve", "bbs_var_plan_destroy", "bbs_var_tune",
+                     "bbs_var_plan_describe",
                      "bbs_mlp_create", "bbs_mlp_destroy", "bbs_mlp_param_count", "bbs_mlp_get_params",
                      "bbs_mlp_set_params", "bbs_mlp_get_grads", "bbs_mlp_observe",
                      "bbs_mlp_finalize_stats", "bbs_mlp_make_samples", "bbs_mlp_gradients",
@@ -455,6 +464,11 @@ class VarPlan:
         st = stream if stream is not None else torch.cuda.current_stream(b.device)
         _check(lib().bbs_var_solve(self._p, _ptr(b), _ptr(x), C.byref(lg), C.c_void_p(st.cuda_stream)),
                "bbs_var_solve")
+
+    def describe(self) -> dict:
+        d = bbs_var_plan_desc()
+        _check(lib().bbs_var_plan_describe(self._p, C.byref(d)), "bbs_var_plan_describe")
+        return {f: getattr(d, f) for f, _ in d._fields_}
 
     def close(self):
         if self._p:

@@ -1,10 +1,12 @@
-// Uneven batches, host side: plan, autotuner and CUDA-graph capture of the
-// persistent launch (kernel in bbs_varsize.cuh).
+// Uneven batches, host side: plan, autotuner and the CUDA graph of the
+// persistent team launch (kernel in bbs_varsize.cuh) and of the packed
+// small-system launches (bbs_varpacked.cuh).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <vector>
 
@@ -12,9 +14,25 @@
 
 #include "../../include/bbs.h"
 #include "bbs_internal.h"
+#include "bbs_kernels.h"
+#include "bbs_varpacked.cuh"
 #include "bbs_varsize.cuh"
 
+namespace bbs {
+const void* varpacked_fn(int solver, int L, int R) {
+    return L == 4 ? varpacked_fn_l4(solver, R) : L == 8 ? varpacked_fn_l8(solver, R) : varpacked_fn_l16(solver, R);
+}
+}  // namespace bbs
+
 // ------------------------------------------------------------------ host
+
+struct PackedClass {
+    int L = 0, R = 0, grid = 0;
+    size_t smem = 0;
+    const void* fn = nullptr;
+    bbs::VarPackedParams P{};
+    cudaGraphNode_t node = nullptr;
+};
 
 struct bbs_var_plan {
     int device = 0;
@@ -23,9 +41,15 @@ struct bbs_var_plan {
     size_t smem = 0;
     const void* fn = nullptr;
     bbs::VarParams P{};
+    int team_count = 0;  // systems of the persistent launch
+    bool has_team = false;
+    int packed_count = 0;
+    std::vector<PackedClass> classes;
     int32_t* d_order = nullptr;
     int32_t* d_counters = nullptr;
-    cudaStream_t capture = nullptr;
+    int32_t* d_tables = nullptr;  // flag [4] | xcols | xsrc of the packed patterns
+    int64_t* d_tab_off = nullptr;
+    int32_t* d_tab_k = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t knode = nullptr;
@@ -95,6 +119,7 @@ bbs_status check_tuning(const bbs_var_tuning* t) {
             return errf(BBS_ERR_INVALID_ARG, "team_warps must be 1, 2, 4, 8 or 16");
         if (t->stage_values[b] != 0 && t->stage_values[b] != 1)
             return errf(BBS_ERR_INVALID_ARG, "stage_values must be 0 or 1");
+        if (t->pack[b] != 0 && t->pack[b] != 1) return errf(BBS_ERR_INVALID_ARG, "pack must be 0 or 1");
     }
     return BBS_OK;
 }
@@ -108,6 +133,73 @@ struct PlanInputs {
     int nsubset;
 };
 
+// Packed small systems (bbs_varpacked.cuh): a class (L, R) per pattern,
+// chosen by the rule of the uniform packed kernels: the narrowest group of 4,
+// 8 or 16 lanes that covers n in at most kMaxPackedR rows per lane and leaves
+// at least kVarPackedMinWarps one-warp blocks resident per SM.
+constexpr int kVarPackMaxN = 16 * bbs::kMaxPackedR;
+constexpr int kVarPackedMinWarps = 8;
+
+struct PatPack {
+    int state = 0;  // 0 not examined, 1 packed, 2 left to the teams
+    int L = 0, R = 0, k = 0;
+    size_t raw = 0;  // shared-memory bytes of one group before the bank shift
+};
+
+size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// A group's bytes padded to 8 L past a multiple of 128, so that the groups of
+// a warp start on different shared-memory banks.
+size_t group_slice(size_t raw, int L) {
+    const size_t shift = (size_t)(8 * L) % 128;
+    return ((raw + 128 - shift + 127) & ~(size_t)127) - 128 + shift;
+}
+
+// One-warp blocks an SM holds: the register cap of the kernel's launch bounds
+// and shared memory (1 KB reserved per block).
+int packed_resident(size_t smem, int R) {
+    const size_t sm_bytes = 228 * 1024;
+    const int by_smem = smem + 1024 > sm_bytes ? 0 : (int)(sm_bytes / (smem + 1024));
+    return std::min(by_smem, bbs::packed_min_blocks(R));
+}
+
+// Reads pattern p's row pointers (the ELL width k is its longest row) and
+// picks its class; a pattern whose row pointers do not ascend within
+// [0, nnz] is rejected.
+bbs_status decide_pattern(const bbs_var_batch* vb, int p, int n, int nnz, int64_t rp_off, int optin,
+                          PatPack& pp) {
+    std::vector<int32_t> rp(n + 1);
+    cudaError_t e = cudaMemcpy(rp.data(), vb->row_ptrs + rp_off, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(e, "pattern row pointers");
+    int k = 0;
+    for (int r = 0; r < n; ++r) {
+        if (rp[r] < 0 || rp[r + 1] < rp[r] || rp[r + 1] > nnz)
+            return errf(BBS_ERR_INVALID_ARG, "pattern %d: row pointers must ascend within [0, nnz]", p);
+        k = std::max(k, rp[r + 1] - rp[r]);
+    }
+    pp.state = 2;
+    const int n_pad = (n + 1) & ~1;
+    for (int L = 4; L <= 16; L *= 2) {
+        const int R = (n + L - 1) / L;
+        if (R > bbs::kMaxPackedR) continue;
+        const size_t raw = align16((size_t)2 * n_pad * 8) + align16((size_t)k * n * 8);
+        const size_t smem = group_slice(raw, L) * (size_t)(32 / L);
+        if (smem > (size_t)optin || packed_resident(smem, R) < kVarPackedMinWarps) continue;
+        pp.state = 1;
+        pp.L = L;
+        pp.R = R;
+        pp.k = k;
+        pp.raw = raw;
+        break;
+    }
+    return BBS_OK;
+}
+
+bbs_status plan_fail(bbs_var_plan* pl, bbs_status s) {
+    bbs_var_plan_destroy(pl);
+    return s;
+}
+
 bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
     const bbs_var_batch* vb = in.vb;
     const bbs_var_tuning& t = in.t;
@@ -115,18 +207,52 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
     const int nb = in.subset ? in.nsubset : vb->num_batch;
     std::vector<int> sys(nb);
     for (int i = 0; i < nb; ++i) sys[i] = in.subset ? in.subset[i] : i;
+    const int dev = bbs::handle_device(h);
+    int sms = 0, optin = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 
-    // team warps per bucket: at least what the rows need, never more than a larger bucket's
     const int B = t.num_buckets;
-    std::vector<int> nmax(B, 0), W(B), bucket(nb);
+    std::vector<int> bucket(nb);
+    std::vector<double> cost(nb);
     for (int i = 0; i < nb; ++i) {
-        const int n = in.host->pat_n[in.host->sys_pattern[sys[i]]];
+        const int p = in.host->sys_pattern[sys[i]];
+        const int n = in.host->pat_n[p];
         int b = 0;
         while (b < B && n > t.bucket_max_n[b]) ++b;
         if (b == B) return errf(BBS_ERR_INVALID_ARG, "system %d (n = %d) exceeds the last bucket", sys[i], n);
         bucket[i] = b;
-        nmax[b] = std::max(nmax[b], n);
+        const double nn = n, nz = in.host->pat_nnz[p];
+        cost[i] = (2.0 * nz + 14.0 * nn) * std::sqrt(nn);
     }
+
+    // which systems run packed (their bucket allows it and their pattern's group fits)
+    std::vector<PatPack> pat(vb->num_patterns);
+    std::vector<int64_t> rp_off;
+    std::vector<char> packed(nb, 0);
+    for (int i = 0; i < nb; ++i) {
+        const int p = in.host->sys_pattern[sys[i]];
+        const int n = in.host->pat_n[p];
+        if (!t.pack[bucket[i]] || n > kVarPackMaxN) continue;
+        if (pat[p].state == 0) {
+            if (rp_off.empty()) {
+                rp_off.resize(vb->num_patterns);
+                cudaError_t e = cudaMemcpy(rp_off.data(), vb->pat_rp_off, sizeof(int64_t) * vb->num_patterns,
+                                           cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) return cuda_err(e, "pattern offsets");
+            }
+            bbs_status s = decide_pattern(vb, p, n, in.host->pat_nnz[p], rp_off[p], optin, pat[p]);
+            if (s != BBS_OK) return s;
+        }
+        packed[i] = pat[p].state == 1;
+    }
+    std::vector<int> team;
+    for (int i = 0; i < nb; ++i)
+        if (!packed[i]) team.push_back(i);
+
+    // team warps per bucket: at least what the rows need, never more than a larger bucket's
+    std::vector<int> nmax(B, 0), W(B);
+    for (int i : team) nmax[bucket[i]] = std::max(nmax[bucket[i]], in.host->pat_n[in.host->sys_pattern[sys[i]]]);
     for (int b = 0; b < B; ++b) {
         const int need = pow2_at_least((std::max(nmax[b], 1) + 32 * rmax - 1) / (32 * rmax));
         W[b] = std::max(t.team_warps[b], need);
@@ -137,15 +263,8 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
             return errf(BBS_ERR_UNSUPPORTED, "bucket %d needs %d warps per system, the block has %d", b, W[b],
                         t.block_warps);
 
-    // order: team size descending, staging, then estimated cost descending
-    std::vector<double> cost(nb);
-    for (int i = 0; i < nb; ++i) {
-        const int p = in.host->sys_pattern[sys[i]];
-        const double n = in.host->pat_n[p], nz = in.host->pat_nnz[p];
-        cost[i] = (2.0 * nz + 14.0 * n) * std::sqrt(n);
-    }
-    std::vector<int> idx(nb);
-    std::iota(idx.begin(), idx.end(), 0);
+    // team order: team size descending, staging, then estimated cost descending
+    std::vector<int> idx = team;
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) {
         const int wa = W[bucket[a]], wc = W[bucket[c]];
         if (wa != wc) return wa > wc;
@@ -155,13 +274,16 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
     });
 
     bbs_var_plan* pl = new bbs_var_plan();
+    pl->device = dev;
+    pl->num_batch = nb;
     bbs::VarParams& P = pl->P;
     P.num_segments = 0;
-    std::vector<int32_t> order(nb);
+    std::vector<int32_t> order;
+    order.reserve(nb);
     std::vector<int> seg_nmax, seg_nnzmax;
-    for (int k = 0; k < nb; ++k) {
+    for (int k = 0; k < (int)idx.size(); ++k) {
         const int i = idx[k];
-        order[k] = sys[i];
+        order.push_back(sys[i]);
         const int w = W[bucket[i]], st = t.stage_values[bucket[i]];
         const int p = in.host->sys_pattern[sys[i]];
         if (P.num_segments == 0 || P.seg_warps[P.num_segments - 1] != w ||
@@ -183,45 +305,78 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
         seg_nmax[s] = std::max(seg_nmax[s], in.host->pat_n[p]);
         seg_nnzmax[s] = std::max(seg_nnzmax[s], in.host->pat_nnz[p]);
     }
-    // per-warp shared-memory slice: a team of w warps uses w consecutive slices
-    size_t slice = 16;
-    for (int s = 0; s < P.num_segments; ++s) {
-        const size_t npad = (size_t)((seg_nmax[s] + 1) & ~1);
-        size_t need = 16 + (256 + 2 * npad) * 8;
-        if (P.seg_stage[s]) need += ((size_t)seg_nnzmax[s] * 8 + 15) / 16 * 16;
-        const size_t per = (need + P.seg_warps[s] - 1) / P.seg_warps[s];
-        slice = std::max(slice, (per + 15) / 16 * 16);
+    pl->team_count = (int)idx.size();
+
+    // packed classes, each ordered by estimated cost (similar systems share a warp)
+    std::map<std::pair<int, int>, std::vector<int>> cls;
+    for (int i = 0; i < nb; ++i)
+        if (packed[i]) {
+            const PatPack& pp = pat[in.host->sys_pattern[sys[i]]];
+            cls[{pp.L, pp.R}].push_back(i);
+        }
+    std::vector<int> class_begin;
+    for (auto& kv : cls) {
+        std::vector<int>& m = kv.second;
+        std::stable_sort(m.begin(), m.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+        class_begin.push_back((int)order.size());
+        PackedClass c;
+        c.L = kv.first.first;
+        c.R = kv.first.second;
+        size_t raw = 16;
+        for (int i : m) {
+            order.push_back(sys[i]);
+            raw = std::max(raw, pat[in.host->sys_pattern[sys[i]]].raw);
+        }
+        c.P.count = (int)m.size();
+        c.P.slice = (int)group_slice(raw, c.L);
+        c.smem = (size_t)c.P.slice * (size_t)(32 / c.L);
+        c.grid = (c.P.count + 32 / c.L - 1) / (32 / c.L);
+        c.fn = bbs::varpacked_fn(in.o->solver == BBS_SOLVER_CG ? 1 : 0, c.L, c.R);
+        pl->packed_count += c.P.count;
+        pl->classes.push_back(c);
     }
-    pl->rmax = rmax;
-    pl->threads = 32 * t.block_warps;
-    pl->smem = slice * (size_t)t.block_warps;
-    P.slice_bytes = (int)slice;
-    int dev = bbs::handle_device(h), sms = 0, optin = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (pl->smem > (size_t)optin) {
-        delete pl;
-        return errf(BBS_ERR_UNSUPPORTED, "the plan needs %zu bytes of shared memory per block (max %d)",
-                    pl->smem, optin);
-    }
-    pl->device = dev;
-    pl->num_batch = nb;
-    pl->fn = rmax == 8 ? bbs::varsize_kernel8_fn() : bbs::varsize_kernel4_fn();
+    pl->has_team = pl->team_count > 0 || pl->classes.empty();
+
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(pl->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem)) !=
-        cudaSuccess) {
-        delete pl;
-        return cuda_err(e, "cudaFuncSetAttribute");
+    if (pl->has_team) {
+        // per-warp shared-memory slice: a team of w warps uses w consecutive slices
+        size_t slice = 16;
+        for (int s = 0; s < P.num_segments; ++s) {
+            const size_t npad = (size_t)((seg_nmax[s] + 1) & ~1);
+            size_t need = 16 + (256 + 2 * npad) * 8;
+            if (P.seg_stage[s]) need += ((size_t)seg_nnzmax[s] * 8 + 15) / 16 * 16;
+            const size_t per = (need + P.seg_warps[s] - 1) / P.seg_warps[s];
+            slice = std::max(slice, (per + 15) / 16 * 16);
+        }
+        pl->rmax = rmax;
+        pl->threads = 32 * t.block_warps;
+        pl->smem = slice * (size_t)t.block_warps;
+        P.slice_bytes = (int)slice;
+        if (pl->smem > (size_t)optin) {
+            delete pl;
+            return errf(BBS_ERR_UNSUPPORTED, "the plan needs %zu bytes of shared memory per block (max %d)",
+                        pl->smem, optin);
+        }
+        pl->fn = rmax == 8 ? bbs::varsize_kernel8_fn() : bbs::varsize_kernel4_fn();
+        if ((e = cudaFuncSetAttribute(pl->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem)) !=
+            cudaSuccess) {
+            delete pl;
+            return cuda_err(e, "cudaFuncSetAttribute");
+        }
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl->fn, pl->threads, pl->smem)) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            delete pl;
+            return e != cudaSuccess ? cuda_err(e, "occupancy query")
+                                    : errf(BBS_ERR_UNSUPPORTED, "the persistent block does not fit on an SM");
+        }
+        pl->grid = per_sm * sms;
     }
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl->fn, pl->threads, pl->smem)) !=
-            cudaSuccess ||
-        per_sm < 1) {
-        delete pl;
-        return e != cudaSuccess ? cuda_err(e, "occupancy query")
-                                : errf(BBS_ERR_UNSUPPORTED, "the persistent block does not fit on an SM");
-    }
-    pl->grid = per_sm * sms;
+    for (auto& c : pl->classes)
+        if ((e = cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem)) !=
+            cudaSuccess)
+            return plan_fail(pl, cuda_err(e, "cudaFuncSetAttribute (packed)"));
 
     P.pat_n = vb->pat_n;
     P.pat_nnz = vb->pat_nnz;
@@ -244,46 +399,107 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
     P.cfg.ws = nullptr;
 
     if ((e = cudaMalloc(&pl->d_order, sizeof(int32_t) * std::max(nb, 1))) != cudaSuccess ||
-        (e = cudaMalloc(&pl->d_counters, sizeof(int32_t) * bbs::kMaxSeg)) != cudaSuccess) {
-        bbs_var_plan_destroy(pl);
-        return errf(BBS_ERR_NO_MEMORY, "plan buffers: %s", cudaGetErrorString(e));
-    }
+        (e = cudaMalloc(&pl->d_counters, sizeof(int32_t) * bbs::kMaxSeg)) != cudaSuccess)
+        return plan_fail(pl, errf(BBS_ERR_NO_MEMORY, "plan buffers: %s", cudaGetErrorString(e)));
     if (nb > 0 && (e = cudaMemcpy(pl->d_order, order.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice)) !=
-                      cudaSuccess) {
-        bbs_var_plan_destroy(pl);
-        return cuda_err(e, "order upload");
-    }
+                      cudaSuccess)
+        return plan_fail(pl, cuda_err(e, "order upload"));
     P.order = pl->d_order;
     P.counters = pl->d_counters;
 
-    // graph: reset the counters, then the persistent launch
-    if ((e = cudaStreamCreateWithFlags(&pl->capture, cudaStreamNonBlocking)) != cudaSuccess) {
-        bbs_var_plan_destroy(pl);
-        return cuda_err(e, "capture stream");
-    }
-    e = cudaStreamBeginCapture(pl->capture, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaMemsetAsync(pl->d_counters, 0, sizeof(int32_t) * bbs::kMaxSeg, pl->capture);
-        void* args[] = {&P};
-        cudaLaunchKernel(pl->fn, dim3(pl->grid), dim3(pl->threads), args, pl->smem, pl->capture);
-        e = cudaStreamEndCapture(pl->capture, &pl->graph);
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
-    if (e == cudaSuccess) {
-        size_t count = 0;
-        cudaGraphGetNodes(pl->graph, nullptr, &count);
-        std::vector<cudaGraphNode_t> nodes(count);
-        cudaGraphGetNodes(pl->graph, nodes.data(), &count);
-        for (auto nd : nodes) {
-            cudaGraphNodeType ty;
-            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) pl->knode = nd;
+    if (!pl->classes.empty()) {
+        // ELL tables of the packed patterns, built on the device once
+        std::vector<int64_t> tab_off(vb->num_patterns, 0);
+        std::vector<int32_t> tab_k(vb->num_patterns, 0);
+        int64_t total = 0;
+        for (int p = 0; p < vb->num_patterns; ++p)
+            if (pat[p].state == 1) {
+                tab_off[p] = total;
+                tab_k[p] = pat[p].k;
+                total += (int64_t)pat[p].k * in.host->pat_n[p];
+            }
+        if ((e = cudaMalloc(&pl->d_tables, sizeof(int32_t) * (size_t)(4 + 2 * total))) != cudaSuccess ||
+            (e = cudaMalloc(&pl->d_tab_off, sizeof(int64_t) * vb->num_patterns)) != cudaSuccess ||
+            (e = cudaMalloc(&pl->d_tab_k, sizeof(int32_t) * vb->num_patterns)) != cudaSuccess)
+            return plan_fail(pl, errf(BBS_ERR_NO_MEMORY, "packed tables: %s", cudaGetErrorString(e)));
+        if ((e = cudaMemcpy(pl->d_tab_off, tab_off.data(), sizeof(int64_t) * vb->num_patterns,
+                            cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(pl->d_tab_k, tab_k.data(), sizeof(int32_t) * vb->num_patterns,
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return plan_fail(pl, cuda_err(e, "packed table upload"));
+        int32_t* flag = pl->d_tables;
+        int32_t* xcols = pl->d_tables + 4;
+        int32_t* xsrc = xcols + total;
+        cudaStream_t st;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
+            return plan_fail(pl, cuda_err(e, "table stream"));
+        std::vector<int64_t> ci_off(vb->num_patterns);
+        e = cudaMemcpy(ci_off.data(), vb->pat_ci_off, sizeof(int64_t) * vb->num_patterns, cudaMemcpyDeviceToHost);
+        for (int p = 0; p < vb->num_patterns && e == cudaSuccess; ++p)
+            if (pat[p].state == 1 && pat[p].k > 0)
+                e = bbs::launch_csr_ell_tables(in.host->pat_n[p], pat[p].k, vb->row_ptrs + rp_off[p],
+                                               vb->col_idxs + ci_off[p], xcols + tab_off[p], xsrc + tab_off[p],
+                                               flag, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+        if (e != cudaSuccess) return plan_fail(pl, cuda_err(e, "packed tables"));
+        for (size_t c = 0; c < pl->classes.size(); ++c) {
+            bbs::VarPackedParams& Q = pl->classes[c].P;
+            Q.pat_n = vb->pat_n;
+            Q.rp_off = vb->pat_rp_off;
+            Q.ci_off = vb->pat_ci_off;
+            Q.row_ptrs = vb->row_ptrs;
+            Q.col_idxs = vb->col_idxs;
+            Q.sys_pattern = vb->sys_pattern;
+            Q.val_off = vb->val_off;
+            Q.vec_off = vb->vec_off;
+            Q.values = vb->values;
+            Q.tab_off = pl->d_tab_off;
+            Q.tab_k = pl->d_tab_k;
+            Q.xcols = xcols;
+            Q.xsrc = xsrc;
+            Q.order = pl->d_order + class_begin[c];
+            Q.cfg = P.cfg;
         }
-        if (pl->knode == nullptr) e = cudaErrorInvalidValue;
     }
-    if (e != cudaSuccess) {
-        bbs_var_plan_destroy(pl);
-        return cuda_err(e, "graph capture");
+
+    // graph: [reset the work counters -> the persistent launch] beside one
+    // launch per packed class (no order among them)
+    if ((e = cudaGraphCreate(&pl->graph, 0)) != cudaSuccess) return plan_fail(pl, cuda_err(e, "graph create"));
+    if (pl->has_team) {
+        cudaMemsetParams mp{};
+        mp.dst = pl->d_counters;
+        mp.elementSize = sizeof(int32_t);
+        mp.width = bbs::kMaxSeg;
+        mp.height = 1;
+        mp.value = 0;
+        mp.pitch = 0;
+        cudaGraphNode_t mset = nullptr;
+        if ((e = cudaGraphAddMemsetNode(&mset, pl->graph, nullptr, 0, &mp)) != cudaSuccess)
+            return plan_fail(pl, cuda_err(e, "graph memset node"));
+        void* args[] = {&P};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(pl->fn);
+        kp.gridDim = dim3(pl->grid);
+        kp.blockDim = dim3(pl->threads);
+        kp.sharedMemBytes = (unsigned)pl->smem;
+        kp.kernelParams = args;
+        if ((e = cudaGraphAddKernelNode(&pl->knode, pl->graph, &mset, 1, &kp)) != cudaSuccess)
+            return plan_fail(pl, cuda_err(e, "graph kernel node"));
     }
+    for (auto& c : pl->classes) {
+        void* args[] = {&c.P};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(c.fn);
+        kp.gridDim = dim3(c.grid);
+        kp.blockDim = dim3(32);
+        kp.sharedMemBytes = (unsigned)c.smem;
+        kp.kernelParams = args;
+        if ((e = cudaGraphAddKernelNode(&c.node, pl->graph, nullptr, 0, &kp)) != cudaSuccess)
+            return plan_fail(pl, cuda_err(e, "graph packed node"));
+    }
+    if ((e = cudaGraphInstantiate(&pl->exec, pl->graph, 0)) != cudaSuccess)
+        return plan_fail(pl, cuda_err(e, "graph instantiate"));
     *out = pl;
     return BBS_OK;
 }
@@ -296,6 +512,7 @@ void default_tuning(int32_t max_n, bbs_var_tuning* t) {
         t->bucket_max_n[b] = e;
         t->team_warps[b] = pow2_at_least((e + 32 * 5 - 1) / (32 * 5));
         t->stage_values[b] = 0;
+        t->pack[b] = 1;
         ++b;
         if (e >= max_n) break;
     }
@@ -337,22 +554,50 @@ bbs_status bbs_var_solve(bbs_var_plan* pl, const double* b, double* x, const bbs
         return errf(BBS_ERR_INVALID_ARG, "null plan or log arrays");
     if (pl->num_batch > 0 && (b == nullptr || x == nullptr)) return errf(BBS_ERR_INVALID_ARG, "null b or x");
     cudaSetDevice(pl->device);
-    pl->P.b = b;
-    pl->P.x = x;
-    pl->P.iters = log->iters;
-    pl->P.rel_res = log->rel_res;
-    pl->P.status = log->status;
-    void* args[] = {&pl->P};
-    cudaKernelNodeParams kp{};
-    kp.func = const_cast<void*>(pl->fn);
-    kp.gridDim = dim3(pl->grid);
-    kp.blockDim = dim3(pl->threads);
-    kp.sharedMemBytes = (unsigned)pl->smem;
-    kp.kernelParams = args;
-    cudaError_t e = cudaGraphExecKernelNodeSetParams(pl->exec, pl->knode, &kp);
-    if (e != cudaSuccess) return cuda_err(e, "graph parameter update");
+    cudaError_t e;
+    if (pl->has_team) {
+        pl->P.b = b;
+        pl->P.x = x;
+        pl->P.iters = log->iters;
+        pl->P.rel_res = log->rel_res;
+        pl->P.status = log->status;
+        void* args[] = {&pl->P};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(pl->fn);
+        kp.gridDim = dim3(pl->grid);
+        kp.blockDim = dim3(pl->threads);
+        kp.sharedMemBytes = (unsigned)pl->smem;
+        kp.kernelParams = args;
+        if ((e = cudaGraphExecKernelNodeSetParams(pl->exec, pl->knode, &kp)) != cudaSuccess)
+            return cuda_err(e, "graph parameter update");
+    }
+    for (auto& c : pl->classes) {
+        c.P.b = b;
+        c.P.x = x;
+        c.P.iters = log->iters;
+        c.P.rel_res = log->rel_res;
+        c.P.status = log->status;
+        void* args[] = {&c.P};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(c.fn);
+        kp.gridDim = dim3(c.grid);
+        kp.blockDim = dim3(32);
+        kp.sharedMemBytes = (unsigned)c.smem;
+        kp.kernelParams = args;
+        if ((e = cudaGraphExecKernelNodeSetParams(pl->exec, c.node, &kp)) != cudaSuccess)
+            return cuda_err(e, "graph parameter update (packed)");
+    }
     if ((e = cudaGraphLaunch(pl->exec, reinterpret_cast<cudaStream_t>(stream))) != cudaSuccess)
         return cuda_err(e, "graph launch");
+    return BBS_OK;
+}
+
+bbs_status bbs_var_plan_describe(const bbs_var_plan* pl, bbs_var_plan_desc* d) {
+    if (pl == nullptr || d == nullptr) return errf(BBS_ERR_INVALID_ARG, "null plan or description");
+    d->team_systems = pl->team_count;
+    d->packed_systems = pl->packed_count;
+    d->packed_launches = (int32_t)pl->classes.size();
+    d->persistent_grid = pl->has_team ? pl->grid : 0;
     return BBS_OK;
 }
 
@@ -362,9 +607,11 @@ bbs_status bbs_var_plan_destroy(bbs_var_plan* pl) {
     cudaDeviceSynchronize();
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
-    if (pl->capture) cudaStreamDestroy(pl->capture);
     if (pl->d_order) cudaFree(pl->d_order);
     if (pl->d_counters) cudaFree(pl->d_counters);
+    if (pl->d_tables) cudaFree(pl->d_tables);
+    if (pl->d_tab_off) cudaFree(pl->d_tab_off);
+    if (pl->d_tab_k) cudaFree(pl->d_tab_k);
     delete pl;
     return BBS_OK;
 }
@@ -428,6 +675,35 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
     cudaEventCreate(&e1);
     bbs_log lg{dit, drr, dst, nullptr};
 
+    // per-system time of one launch choice on bucket k's sample (INFINITY if
+    // the choice cannot be planned)
+    auto trial = [&](int k, int bw, int w, int stg, int pack) -> double {
+        PlanInputs in{vb, host, o, {}, samp[k].data(), (int)samp[k].size()};
+        std::memset(&in.t, 0, sizeof in.t);
+        in.t.num_buckets = 1;
+        in.t.bucket_max_n[0] = 2048;
+        in.t.team_warps[0] = w;
+        in.t.stage_values[0] = stg;
+        in.t.pack[0] = pack;
+        in.t.block_warps = bw;
+        bbs_var_plan* pl = nullptr;
+        if (build_plan(h, in, &pl) != BBS_OK) return INFINITY;
+        float ms_sum = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            cudaMemcpyAsync(dx, x0, sizeof(double) * vec_len, cudaMemcpyDeviceToDevice, st);
+            cudaEventRecord(e0, st);
+            ok = bbs_var_solve(pl, b, dx, &lg, st) == BBS_OK;
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_sum += ms;
+        }
+        bbs_var_plan_destroy(pl);
+        return ok ? ms_sum / 2.0 / samp[k].size() : INFINITY;
+    };
+
     bbs_var_tuning best_overall = base;
     double best_total = INFINITY;
     for (int bw : {8, 16}) {
@@ -438,42 +714,29 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
         bool feasible = true;
         for (int k = 0; k < B && feasible; ++k) {
             if (samp[k].empty()) continue;
-            int nk = 0;
-            for (int i : samp[k]) nk = std::max(nk, host->pat_n[host->sys_pattern[i]]);
+            int nk = 0, nmin = 1 << 30;
+            for (int i : samp[k]) {
+                nk = std::max(nk, host->pat_n[host->sys_pattern[i]]);
+                nmin = std::min(nmin, host->pat_n[host->sys_pattern[i]]);
+            }
             const int wmin = pow2_at_least((nk + 32 * rmax - 1) / (32 * rmax));
             double best = INFINITY;
-            int bestw = wmin, bests = 0;
-            for (int w = wmin; w <= bw; w *= 2) {
+            int bestw = wmin, bests = 0, bestp = 0;
+            for (int w = wmin; w <= bw; w *= 2)
                 for (int stg = 0; stg <= 1; ++stg) {
-                    PlanInputs in{vb, host, o, {}, samp[k].data(), (int)samp[k].size()};
-                    std::memset(&in.t, 0, sizeof in.t);
-                    in.t.num_buckets = 1;
-                    in.t.bucket_max_n[0] = 2048;
-                    in.t.team_warps[0] = w;
-                    in.t.stage_values[0] = stg;
-                    in.t.block_warps = bw;
-                    bbs_var_plan* pl = nullptr;
-                    if (build_plan(h, in, &pl) != BBS_OK) continue;
-                    float ms_sum = 0.f;
-                    bool ok = true;
-                    for (int rep = 0; rep < 3 && ok; ++rep) {
-                        cudaMemcpyAsync(dx, x0, sizeof(double) * vec_len, cudaMemcpyDeviceToDevice, st);
-                        cudaEventRecord(e0, st);
-                        ok = bbs_var_solve(pl, b, dx, &lg, st) == BBS_OK;
-                        cudaEventRecord(e1, st);
-                        cudaEventSynchronize(e1);
-                        float ms = 0.f;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        if (rep > 0) ms_sum += ms;
-                    }
-                    bbs_var_plan_destroy(pl);
-                    if (!ok) continue;
-                    const double per = ms_sum / 2.0 / samp[k].size();
+                    const double per = trial(k, bw, w, stg, 0);
                     if (per < best) {
                         best = per;
                         bestw = w;
                         bests = stg;
                     }
+                }
+            // packing the bucket's small systems, the rest as the best team choice
+            if (nmin <= kVarPackMaxN) {
+                const double per = trial(k, bw, bestw, bests, 1);
+                if (per < best) {
+                    best = per;
+                    bestp = 1;
                 }
             }
             if (!std::isfinite(best)) {
@@ -482,6 +745,7 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
             }
             cand.team_warps[k] = bestw;
             cand.stage_values[k] = bests;
+            cand.pack[k] = bestp;
             total += best * members[k].size();
         }
         if (feasible && total < best_total) {

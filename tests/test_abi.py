@@ -82,6 +82,38 @@ def test_struct_layouts_match_header():
     assert C.sizeof(bbs.bbs_launch_info) == 40 and bbs.bbs_launch_info.smem_bytes.offset == 24
 
 
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets that a
+    C compiler gives the header's declaration."""
+    import ctypes as C
+    import shutil
+    import subprocess
+
+    from paper_2308_08417_gb300 import bbs
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [bbs.bbs_options, bbs.bbs_batch_matrix, bbs.bbs_log, bbs.bbs_launch_info, bbs.bbs_var_batch,
+               bbs.bbs_var_host_info, bbs.bbs_var_tuning, bbs.bbs_var_plan_desc]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "bbs.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'    printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
+        for f, _ in st._fields_:
+            lines.append(f'    printf("{st.__name__} {f} %zu\\n", offsetof({st.__name__}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for st in structs:
+        assert got[(st.__name__, "size")] == C.sizeof(st), st.__name__
+        for f, _ in st._fields_:
+            assert got[(st.__name__, f)] == getattr(st, f).offset, f"{st.__name__}.{f}"
+
+
 def test_host_chunk_plan():
     """bbs_solve_host's chunks: in order, the batch covered once, at least
     2,048 systems each but the last, led by a quarter and a half chunk, about

@@ -39,8 +39,9 @@ def run_plan(bbs, plan, vb):
     return x.cpu().numpy(), log.iters.cpu().numpy(), log.rel_res.cpu().numpy(), log.status.cpu().numpy()
 
 
-def check_against_oracle(vb, got, solver="bicgstab", sample=400):
-    idx = np.random.default_rng(11).choice(vb.num_batch, min(sample, vb.num_batch), replace=False)
+def check_against_oracle(vb, got, solver="bicgstab", sample=400, idx=None):
+    if idx is None:
+        idx = np.random.default_rng(11).choice(vb.num_batch, min(sample, vb.num_batch), replace=False)
     xr, itr, relr, str_ = oracle.solve_varsize(vb, solver=solver, systems=idx)
     x, it, rel, st = got
     fails = []
@@ -72,6 +73,7 @@ def test_tuned_plans_match_oracle(bbs, handle, uneven):
     tuning = bbs.bbs_var_tune(handle, vbd, b, x0, opts, sample=128)
     d = tuning.as_dict()
     assert d["block_warps"] in (8, 16) and all(w in (1, 2, 4, 8, 16) for w in d["team_warps"])
+    assert all(p in (0, 1) for p in d["pack"])
     assert np.array_equal(x0.cpu().numpy(), uneven.x0)  # the tuner leaves x0 alone
     plan = bbs.VarPlan(handle, vbd, opts, tuning)
     got = run_plan(bbs, plan, uneven)
@@ -85,6 +87,7 @@ def test_tuned_plans_match_oracle(bbs, handle, uneven):
             for k in range(t.num_buckets):
                 t.stage_values[k] = stage
                 t.team_warps[k] = min(bw, 2 ** k // 2 or 1)
+                t.pack[k] = 0
             plan = bbs.VarPlan(handle, vbd, opts, t)
             got = run_plan(bbs, plan, uneven)
             fails = check_against_oracle(uneven, got, sample=150)
@@ -121,3 +124,70 @@ def test_plan_argument_errors(bbs, handle, uneven):
     t = bbs.bbs_var_default_tuning(256)  # buckets stop at 256: larger systems rejected
     with pytest.raises(bbs.BBSError):
         bbs.VarPlan(handle, vbd, bbs.bbs_default_options(), t)
+
+
+def test_packed_small_systems(bbs, handle, uneven):
+    """By default the small systems run packed: groups of 4, 8 or 16 lanes,
+    each with its own pattern, share a warp in lockstep. Every packable system
+    (n <= 160) meets the oracle bar; with packing off every system runs on a
+    team and meets it too, with the same statuses."""
+    vbd = bbs.VarDeviceBatch.from_varbatch(uneven)
+    opts = bbs.bbs_default_options()
+    plan = bbs.VarPlan(handle, vbd, opts)
+    d = plan.describe()
+    n = uneven.sys_n()
+    small = np.nonzero(n <= 160)[0]
+    assert d["team_systems"] + d["packed_systems"] == uneven.num_batch
+    assert 0.8 * len(small) <= d["packed_systems"] <= len(small)
+    assert d["packed_launches"] >= 3 and d["persistent_grid"] > 0
+    got = run_plan(bbs, plan, uneven)
+    assert (got[3] == 0).all()
+    fails = check_against_oracle(uneven, got, idx=small[::2])
+    assert not fails, "\n".join(fails[:10])
+    t = bbs.bbs_var_default_tuning(1024)
+    for k in range(t.num_buckets):
+        t.pack[k] = 0
+    plan0 = bbs.VarPlan(handle, vbd, opts, t)
+    assert plan0.describe()["packed_systems"] == 0
+    got0 = run_plan(bbs, plan0, uneven)
+    assert np.array_equal(got0[3], got[3])
+    fails = check_against_oracle(uneven, got0, idx=small[::4])
+    assert not fails, "\n".join(fails[:10])
+    # graph replay of the packed plan gives the same bits
+    again = run_plan(bbs, plan, uneven)
+    assert np.array_equal(again[0], got[0]) and np.array_equal(again[1], got[1])
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "cg"])
+def test_all_packed_batch(bbs, handle, solver):
+    """A batch of systems of 4 to 64 rows runs packed only (no persistent
+    launch in the graph): one packed launch per (lanes, rows per lane) class,
+    ragged warps at each class's end, BiCGSTAB and CG (symmetrised values)."""
+    vb = W.uneven(1500, n_min=4, n_max=64)
+    if solver == "cg":
+        for pi, p in enumerate(vb.patterns):
+            members = np.nonzero(vb.sys_pattern == pi)[0]
+            if len(members) == 0:
+                continue
+            vals = W.stencil_values(p, len(members), np.random.default_rng(pi), 0.05, 0.5, symmetric=True)
+            for k, i in enumerate(members):
+                vb.values[int(vb.val_off[i]):int(vb.val_off[i]) + p.nnz] = vals[k]
+    vbd = bbs.VarDeviceBatch.from_varbatch(vb)
+    plan = bbs.VarPlan(handle, vbd, bbs.bbs_default_options(solver=solver))
+    d = plan.describe()
+    assert d["packed_systems"] == vb.num_batch and d["team_systems"] == 0 and d["persistent_grid"] == 0
+    got = run_plan(bbs, plan, vb)
+    fails = check_against_oracle(vb, got, solver=solver, sample=500)
+    assert not fails, "\n".join(fails[:10])
+
+
+def test_plan_rejects_broken_row_pointers(bbs, handle):
+    """The planner reads the row pointers of the patterns it packs; a pattern
+    whose row pointers descend is an argument error (nothing is launched)."""
+    vb = W.uneven(200, n_max=64)
+    vbd = bbs.VarDeviceBatch.from_varbatch(vb)
+    p = int(vb.sys_pattern[0])
+    rp_off = int(vbd.tensors["pat_rp_off"][p])
+    vbd.tensors["row_ptrs"][rp_off + 1] = -5
+    with pytest.raises(bbs.BBSError):
+        bbs.VarPlan(handle, vbd, bbs.bbs_default_options())
