@@ -340,12 +340,13 @@ class Uneven:
         self.desc = self.plan.describe()
         self.log = bbs.Log.empty(vb.num_batch, device=dev)
         self.num_batch = vb.num_batch
-        # one graph: the persistent team launch (with its counter reset) and
-        # one launch per packed class of small systems
-        persistent = 1 if self.desc["persistent_grid"] else 0
-        self.kernel = ("varsize_kernel" if not self.desc["packed_launches"]
-                       else "varsize_kernel+varpacked_kernel" if persistent else "varpacked_kernel")
-        self.launches_per_step = persistent + self.desc["packed_launches"]
+        # one graph: the persistent team launch (with its counter reset), one
+        # launch per packed class of small systems and per wide-team class
+        d = self.desc
+        persistent = 1 if d["persistent_grid"] else 0
+        self.kernel = "+".join(k for k, c in (("varsize_kernel", persistent), ("varpacked_kernel", d["packed_launches"]),
+                                              ("varwide_kernel", d["wide_launches"])) if c)
+        self.launches_per_step = persistent + d["packed_launches"] + d["wide_launches"]
         self.mixed = False
 
     def reset(self):

@@ -307,16 +307,21 @@ typedef struct {
  * whether its small systems are packed (pack[b] = 1: a system of at most 160
  * rows whose group fits shared memory is solved by 4, 8 or 16 lanes, with
  * 8, 4 or 2 systems per warp in lockstep, as bbs_solve packs uniform batches;
- * 0: one team per system). block_warps is 8 (up to 8 rows per thread) or 16
- * (up to 4 rows per thread). The planner lowers a bucket's warps to those of
- * the next larger bucket if they exceed them and raises them to the minimum
- * its rows need. */
+ * 0: one team per system), and whether its large systems run as wide teams
+ * (wide[b] = 1, BiCGSTAB with Jacobi only: a system that needs more than 8
+ * rows per thread on the fewest warps that hold it in at most 16 rows per
+ * thread (1, 2 or 4 warps) is solved by that many warps, one block per system,
+ * values staged, in a launch of its own, where such blocks still leave an SM
+ * 8 warps; 0: every team runs in the persistent launch). block_warps is 8 (up to 8 rows per thread) or 16 (up to 4 rows per
+ * thread). The planner lowers a bucket's warps to those of the next larger
+ * bucket if they exceed them and raises them to the minimum its rows need. */
 typedef struct {
     int32_t num_buckets; /* 1..8 */
     int32_t bucket_max_n[8];
     int32_t team_warps[8];
     int32_t stage_values[8];
     int32_t pack[8];
+    int32_t wide[8];
     int32_t block_warps;
     int32_t reserved;
 } bbs_var_tuning;
@@ -325,18 +330,19 @@ typedef struct bbs_var_plan bbs_var_plan;
 
 /* Default tuning: power-of-two buckets up to max_n, one warp per 5 rows per
  * thread (as bbs_default_block_size), values streamed, small systems packed,
- * 8-warp blocks. Host only. */
+ * wide teams in the buckets above 512 rows, 8-warp blocks. Host only. */
 bbs_status bbs_var_default_tuning(int32_t max_n, bbs_var_tuning *tuning);
 
 /* Plan the persistent solve of `batch` (FP64, BiCGSTAB or CG, Jacobi or
  * none). The systems that run packed (see bbs_var_tuning.pack) are grouped by
- * (lanes per system, rows per lane), one launch per group; the planner reads
+ * (lanes per system, rows per lane), one launch per group, and so are the
+ * wide teams (bbs_var_tuning.wide) by (warps, rows per thread); the planner reads
  * their patterns' row pointers (rejecting, with BBS_ERR_INVALID_ARG, row
  * pointers that do not ascend within [0, nnz]) and builds an ELL column table
  * of each such pattern on the device. The other systems are ordered longest
  * first and grouped in segments of equal team size for one persistent launch
  * whose grid fills every SM. The CUDA graph holds "reset the work counters ->
- * the persistent launch" and, beside it, the packed launches. Allocates the
+ * the persistent launch" and, beside it, the packed and wide launches. Allocates the
  * plan's own device buffers (system order, counters, tables). The patterns
  * must not change while the plan lives (values, b and x may). tuning NULL =
  * default tuning. */
@@ -351,13 +357,16 @@ bbs_status bbs_var_solve(bbs_var_plan *plan, const double *b, double *x, const b
                          void *stream);
 
 /* What a plan runs: systems solved by teams in the persistent launch, systems
- * solved packed and the number of packed launches, and the persistent grid
- * (0 when every system is packed). Host only. */
+ * solved packed and the number of packed launches, the persistent grid (0 when
+ * every system runs packed or wide), and systems solved by wide teams and the
+ * number of wide launches. Host only. */
 typedef struct {
     int32_t team_systems;
     int32_t packed_systems;
     int32_t packed_launches;
     int32_t persistent_grid;
+    int32_t wide_systems;
+    int32_t wide_launches;
 } bbs_var_plan_desc;
 
 bbs_status bbs_var_plan_describe(const bbs_var_plan *plan, bbs_var_plan_desc *desc);

@@ -65,18 +65,21 @@ class bbs_var_host_info(C.Structure):
 
 class bbs_var_plan_desc(C.Structure):
     _fields_ = [("team_systems", C.c_int32), ("packed_systems", C.c_int32),
-                ("packed_launches", C.c_int32), ("persistent_grid", C.c_int32)]
+                ("packed_launches", C.c_int32), ("persistent_grid", C.c_int32),
+                ("wide_systems", C.c_int32), ("wide_launches", C.c_int32)]
 
 
 class bbs_var_tuning(C.Structure):
     _fields_ = [("num_buckets", C.c_int32), ("bucket_max_n", C.c_int32 * 8),
                 ("team_warps", C.c_int32 * 8), ("stage_values", C.c_int32 * 8),
-                ("pack", C.c_int32 * 8), ("block_warps", C.c_int32), ("reserved", C.c_int32)]
+                ("pack", C.c_int32 * 8), ("wide", C.c_int32 * 8), ("block_warps", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self) -> dict:
         k = self.num_buckets
         return {"bucket_max_n": list(self.bucket_max_n[:k]), "team_warps": list(self.team_warps[:k]),
                 "stage_values": list(self.stage_values[:k]), "pack": list(self.pack[:k]),
+                "wide": list(self.wide[:k]),
                 "block_warps": self.block_warps}
 
     @classmethod
@@ -89,6 +92,7 @@ class bbs_var_tuning(C.Structure):
             t.team_warps[i] = d["team_warps"][i]
             t.stage_values[i] = d["stage_values"][i]
             t.pack[i] = d.get("pack", [1] * k)[i]
+            t.wide[i] = d.get("wide", [1] * k)[i]
         t.block_warps = d["block_warps"]
         return t
 

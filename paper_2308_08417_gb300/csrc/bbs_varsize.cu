@@ -16,12 +16,14 @@
 #include "bbs_internal.h"
 #include "bbs_kernels.h"
 #include "bbs_varpacked.cuh"
+#include "bbs_varwide.cuh"
 #include "bbs_varsize.cuh"
 
 namespace bbs {
 const void* varpacked_fn(int solver, int L, int R) {
     return L == 4 ? varpacked_fn_l4(solver, R) : L == 8 ? varpacked_fn_l8(solver, R) : varpacked_fn_l16(solver, R);
 }
+const void* varwide_fn(int R) { return R <= 12 ? varwide_fn_lo(R) : varwide_fn_hi(R); }
 }  // namespace bbs
 
 // ------------------------------------------------------------------ host
@@ -31,6 +33,14 @@ struct PackedClass {
     size_t smem = 0;
     const void* fn = nullptr;
     bbs::VarPackedParams P{};
+    cudaGraphNode_t node = nullptr;
+};
+
+struct WideClass {
+    int warps = 0, R = 0;
+    size_t smem = 0;
+    const void* fn = nullptr;
+    bbs::VarWideParams P{};
     cudaGraphNode_t node = nullptr;
 };
 
@@ -45,6 +55,8 @@ struct bbs_var_plan {
     bool has_team = false;
     int packed_count = 0;
     std::vector<PackedClass> classes;
+    int wide_count = 0;
+    std::vector<WideClass> wides;
     int32_t* d_order = nullptr;
     int32_t* d_counters = nullptr;
     int32_t* d_tables = nullptr;  // flag [4] | xcols | xsrc of the packed patterns
@@ -120,6 +132,7 @@ bbs_status check_tuning(const bbs_var_tuning* t) {
         if (t->stage_values[b] != 0 && t->stage_values[b] != 1)
             return errf(BBS_ERR_INVALID_ARG, "stage_values must be 0 or 1");
         if (t->pack[b] != 0 && t->pack[b] != 1) return errf(BBS_ERR_INVALID_ARG, "pack must be 0 or 1");
+        if (t->wide[b] != 0 && t->wide[b] != 1) return errf(BBS_ERR_INVALID_ARG, "wide must be 0 or 1");
     }
     return BBS_OK;
 }
@@ -195,6 +208,17 @@ bbs_status decide_pattern(const bbs_var_batch* vb, int p, int n, int nnz, int64_
     return BBS_OK;
 }
 
+// Warps an SM holds of wide blocks of w warps: the kernel may use 255
+// registers a thread (8 / w blocks), and shared memory (1 KB reserved per
+// block). A wide team is chosen only where this keeps at least the 8 warps a
+// persistent block holds: with fewer, the FP64 pipe idles more than the
+// saved barriers gain (measured on GB300 with 2D 9-point systems).
+int wide_resident_warps(size_t smem, int w) {
+    const size_t sm_bytes = 228 * 1024;
+    const int by_smem = smem + 1024 > sm_bytes ? 0 : (int)(sm_bytes / (smem + 1024));
+    return std::min(by_smem, 8 / w) * w;
+}
+
 bbs_status plan_fail(bbs_var_plan* pl, bbs_status s) {
     bbs_var_plan_destroy(pl);
     return s;
@@ -246,9 +270,28 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
         }
         packed[i] = pat[p].state == 1;
     }
+    // which of the others run as wide teams: a bucket marked wide, BiCGSTAB with
+    // Jacobi, more than 8 rows per thread on the fewest warps that keep them
+    // within kVarWideMaxR, and a block area that fits
+    std::vector<int> wide_w(nb, 0), wide_r(nb, 0);
+    const bool wide_ok = in.o->solver == BBS_SOLVER_BICGSTAB && in.o->precond == BBS_PREC_JACOBI;
     std::vector<int> team;
-    for (int i = 0; i < nb; ++i)
-        if (!packed[i]) team.push_back(i);
+    for (int i = 0; i < nb; ++i) {
+        if (packed[i]) continue;
+        const int p = in.host->sys_pattern[sys[i]];
+        const int n = in.host->pat_n[p];
+        if (wide_ok && t.wide[bucket[i]]) {
+            const int w = pow2_at_least((n + 32 * bbs::kVarWideMaxR - 1) / (32 * bbs::kVarWideMaxR));
+            const int R = (n + 32 * w - 1) / (32 * w);
+            const size_t smem = bbs::varwide_smem(n, in.host->pat_nnz[p]);
+            if (w <= 4 && R >= bbs::kVarWideMinR && smem <= (size_t)optin && wide_resident_warps(smem, w) >= 8) {
+                wide_w[i] = w;
+                wide_r[i] = R;
+                continue;
+            }
+        }
+        team.push_back(i);
+    }
 
     // team warps per bucket: at least what the rows need, never more than a larger bucket's
     std::vector<int> nmax(B, 0), W(B);
@@ -335,7 +378,29 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
         pl->packed_count += c.P.count;
         pl->classes.push_back(c);
     }
-    pl->has_team = pl->team_count > 0 || pl->classes.empty();
+    // wide classes, each ordered by estimated cost (longest first)
+    std::map<std::pair<int, int>, std::vector<int>> wcls;
+    for (int i = 0; i < nb; ++i)
+        if (wide_w[i] > 0) wcls[{wide_w[i], wide_r[i]}].push_back(i);
+    std::vector<int> wide_begin;
+    for (auto& kv : wcls) {
+        std::vector<int>& m = kv.second;
+        std::stable_sort(m.begin(), m.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+        wide_begin.push_back((int)order.size());
+        WideClass c;
+        c.warps = kv.first.first;
+        c.R = kv.first.second;
+        for (int i : m) {
+            order.push_back(sys[i]);
+            const int p = in.host->sys_pattern[sys[i]];
+            c.smem = std::max(c.smem, bbs::varwide_smem(in.host->pat_n[p], in.host->pat_nnz[p]));
+        }
+        c.P.count = (int)m.size();
+        c.fn = bbs::varwide_fn(c.R);
+        pl->wide_count += c.P.count;
+        pl->wides.push_back(c);
+    }
+    pl->has_team = pl->team_count > 0 || (pl->classes.empty() && pl->wides.empty());
 
     cudaError_t e;
     if (pl->has_team) {
@@ -377,6 +442,10 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
         if ((e = cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem)) !=
             cudaSuccess)
             return plan_fail(pl, cuda_err(e, "cudaFuncSetAttribute (packed)"));
+    for (auto& c : pl->wides)
+        if ((e = cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem)) !=
+            cudaSuccess)
+            return plan_fail(pl, cuda_err(e, "cudaFuncSetAttribute (wide)"));
 
     P.pat_n = vb->pat_n;
     P.pat_nnz = vb->pat_nnz;
@@ -406,6 +475,21 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
         return plan_fail(pl, cuda_err(e, "order upload"));
     P.order = pl->d_order;
     P.counters = pl->d_counters;
+    for (size_t c = 0; c < pl->wides.size(); ++c) {
+        bbs::VarWideParams& Q = pl->wides[c].P;
+        Q.pat_n = vb->pat_n;
+        Q.pat_nnz = vb->pat_nnz;
+        Q.rp_off = vb->pat_rp_off;
+        Q.ci_off = vb->pat_ci_off;
+        Q.row_ptrs = vb->row_ptrs;
+        Q.col_idxs = vb->col_idxs;
+        Q.sys_pattern = vb->sys_pattern;
+        Q.val_off = vb->val_off;
+        Q.vec_off = vb->vec_off;
+        Q.values = vb->values;
+        Q.order = pl->d_order + wide_begin[c];
+        Q.cfg = P.cfg;
+    }
 
     if (!pl->classes.empty()) {
         // ELL tables of the packed patterns, built on the device once
@@ -464,7 +548,7 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
     }
 
     // graph: [reset the work counters -> the persistent launch] beside one
-    // launch per packed class (no order among them)
+    // launch per packed class and per wide class (no order among them)
     if ((e = cudaGraphCreate(&pl->graph, 0)) != cudaSuccess) return plan_fail(pl, cuda_err(e, "graph create"));
     if (pl->has_team) {
         cudaMemsetParams mp{};
@@ -498,6 +582,17 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
         if ((e = cudaGraphAddKernelNode(&c.node, pl->graph, nullptr, 0, &kp)) != cudaSuccess)
             return plan_fail(pl, cuda_err(e, "graph packed node"));
     }
+    for (auto& c : pl->wides) {
+        void* args[] = {&c.P};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(c.fn);
+        kp.gridDim = dim3(c.P.count);
+        kp.blockDim = dim3(32 * c.warps);
+        kp.sharedMemBytes = (unsigned)c.smem;
+        kp.kernelParams = args;
+        if ((e = cudaGraphAddKernelNode(&c.node, pl->graph, nullptr, 0, &kp)) != cudaSuccess)
+            return plan_fail(pl, cuda_err(e, "graph wide node"));
+    }
     if ((e = cudaGraphInstantiate(&pl->exec, pl->graph, 0)) != cudaSuccess)
         return plan_fail(pl, cuda_err(e, "graph instantiate"));
     *out = pl;
@@ -513,6 +608,7 @@ void default_tuning(int32_t max_n, bbs_var_tuning* t) {
         t->team_warps[b] = pow2_at_least((e + 32 * 5 - 1) / (32 * 5));
         t->stage_values[b] = 0;
         t->pack[b] = 1;
+        t->wide[b] = e > 512 ? 1 : 0;  // measured: wide teams pay above 512 rows
         ++b;
         if (e >= max_n) break;
     }
@@ -587,6 +683,22 @@ bbs_status bbs_var_solve(bbs_var_plan* pl, const double* b, double* x, const bbs
         if ((e = cudaGraphExecKernelNodeSetParams(pl->exec, c.node, &kp)) != cudaSuccess)
             return cuda_err(e, "graph parameter update (packed)");
     }
+    for (auto& c : pl->wides) {
+        c.P.b = b;
+        c.P.x = x;
+        c.P.iters = log->iters;
+        c.P.rel_res = log->rel_res;
+        c.P.status = log->status;
+        void* args[] = {&c.P};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(c.fn);
+        kp.gridDim = dim3(c.P.count);
+        kp.blockDim = dim3(32 * c.warps);
+        kp.sharedMemBytes = (unsigned)c.smem;
+        kp.kernelParams = args;
+        if ((e = cudaGraphExecKernelNodeSetParams(pl->exec, c.node, &kp)) != cudaSuccess)
+            return cuda_err(e, "graph parameter update (wide)");
+    }
     if ((e = cudaGraphLaunch(pl->exec, reinterpret_cast<cudaStream_t>(stream))) != cudaSuccess)
         return cuda_err(e, "graph launch");
     return BBS_OK;
@@ -597,6 +709,8 @@ bbs_status bbs_var_plan_describe(const bbs_var_plan* pl, bbs_var_plan_desc* d) {
     d->team_systems = pl->team_count;
     d->packed_systems = pl->packed_count;
     d->packed_launches = (int32_t)pl->classes.size();
+    d->wide_systems = pl->wide_count;
+    d->wide_launches = (int32_t)pl->wides.size();
     d->persistent_grid = pl->has_team ? pl->grid : 0;
     return BBS_OK;
 }
@@ -677,7 +791,7 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
 
     // per-system time of one launch choice on bucket k's sample (INFINITY if
     // the choice cannot be planned)
-    auto trial = [&](int k, int bw, int w, int stg, int pack) -> double {
+    auto trial = [&](int k, int bw, int w, int stg, int pack, int wide) -> double {
         PlanInputs in{vb, host, o, {}, samp[k].data(), (int)samp[k].size()};
         std::memset(&in.t, 0, sizeof in.t);
         in.t.num_buckets = 1;
@@ -685,6 +799,7 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
         in.t.team_warps[0] = w;
         in.t.stage_values[0] = stg;
         in.t.pack[0] = pack;
+        in.t.wide[0] = wide;
         in.t.block_warps = bw;
         bbs_var_plan* pl = nullptr;
         if (build_plan(h, in, &pl) != BBS_OK) return INFINITY;
@@ -724,7 +839,7 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
             int bestw = wmin, bests = 0, bestp = 0;
             for (int w = wmin; w <= bw; w *= 2)
                 for (int stg = 0; stg <= 1; ++stg) {
-                    const double per = trial(k, bw, w, stg, 0);
+                    const double per = trial(k, bw, w, stg, 0, 0);
                     if (per < best) {
                         best = per;
                         bestw = w;
@@ -733,10 +848,20 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
                 }
             // packing the bucket's small systems, the rest as the best team choice
             if (nmin <= kVarPackMaxN) {
-                const double per = trial(k, bw, bestw, bests, 1);
+                const double per = trial(k, bw, bestw, bests, 1, 0);
                 if (per < best) {
                     best = per;
                     bestp = 1;
+                }
+            }
+            // wide teams for the bucket's systems that need more than 8 rows per
+            // thread on their fewest warps
+            int bestwide = 0;
+            if (o->solver == BBS_SOLVER_BICGSTAB && o->precond == BBS_PREC_JACOBI && nk > 32 * 8) {
+                const double per = trial(k, bw, bestw, bests, bestp, 1);
+                if (per < best) {
+                    best = per;
+                    bestwide = 1;
                 }
             }
             if (!std::isfinite(best)) {
@@ -746,6 +871,7 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
             cand.team_warps[k] = bestw;
             cand.stage_values[k] = bests;
             cand.pack[k] = bestp;
+            cand.wide[k] = bestwide;
             total += best * members[k].size();
         }
         if (feasible && total < best_total) {

@@ -73,7 +73,7 @@ def test_tuned_plans_match_oracle(bbs, handle, uneven):
     tuning = bbs.bbs_var_tune(handle, vbd, b, x0, opts, sample=128)
     d = tuning.as_dict()
     assert d["block_warps"] in (8, 16) and all(w in (1, 2, 4, 8, 16) for w in d["team_warps"])
-    assert all(p in (0, 1) for p in d["pack"])
+    assert all(p in (0, 1) for p in d["pack"]) and all(w in (0, 1) for w in d["wide"])
     assert np.array_equal(x0.cpu().numpy(), uneven.x0)  # the tuner leaves x0 alone
     plan = bbs.VarPlan(handle, vbd, opts, tuning)
     got = run_plan(bbs, plan, uneven)
@@ -88,6 +88,7 @@ def test_tuned_plans_match_oracle(bbs, handle, uneven):
                 t.stage_values[k] = stage
                 t.team_warps[k] = min(bw, 2 ** k // 2 or 1)
                 t.pack[k] = 0
+                t.wide[k] = 0
             plan = bbs.VarPlan(handle, vbd, opts, t)
             got = run_plan(bbs, plan, uneven)
             fails = check_against_oracle(uneven, got, sample=150)
@@ -137,7 +138,7 @@ def test_packed_small_systems(bbs, handle, uneven):
     d = plan.describe()
     n = uneven.sys_n()
     small = np.nonzero(n <= 160)[0]
-    assert d["team_systems"] + d["packed_systems"] == uneven.num_batch
+    assert d["team_systems"] + d["packed_systems"] + d["wide_systems"] == uneven.num_batch
     assert 0.8 * len(small) <= d["packed_systems"] <= len(small)
     assert d["packed_launches"] >= 3 and d["persistent_grid"] > 0
     got = run_plan(bbs, plan, uneven)
@@ -191,3 +192,41 @@ def test_plan_rejects_broken_row_pointers(bbs, handle):
     vbd.tensors["row_ptrs"][rp_off + 1] = -5
     with pytest.raises(bbs.BBSError):
         bbs.VarPlan(handle, vbd, bbs.bbs_default_options())
+
+
+def test_wide_teams(bbs, handle, uneven):
+    """With wide teams on in every bucket, the systems that need more than 8
+    rows per thread on their fewest warps (n > 256 here) run as wide teams where
+    their blocks leave an SM 8 warps (one block of 1 or 2 warps per system, up
+    to 16 rows per thread, in launches of their own); they meet the oracle bar,
+    and so do the same systems on the persistent launch's teams with wide teams
+    off. The default tuning turns them on above 512 rows."""
+    vbd = bbs.VarDeviceBatch.from_varbatch(uneven)
+    opts = bbs.bbs_default_options()
+    t1 = bbs.bbs_var_default_tuning(1024)
+    assert t1.as_dict()["wide"] == [int(e > 512) for e in t1.as_dict()["bucket_max_n"]]
+    for k in range(t1.num_buckets):
+        t1.wide[k] = 1
+    plan = bbs.VarPlan(handle, vbd, opts, t1)
+    d = plan.describe()
+    n, nnz = uneven.sys_n(), uneven.sys_nnz()
+    w = np.where(n <= 512, 1, 2)
+    smem = (256 + 2 * ((n + 1) & ~1)) * 8 + (nnz * 8 + 15) // 16 * 16
+    fits = np.minimum(228 * 1024 // (smem + 1024), 8 // w) * w >= 8
+    large = np.nonzero((n > 256) & fits)[0]
+    assert d["wide_systems"] == len(large) > 0 and d["wide_launches"] >= 2
+    got = run_plan(bbs, plan, uneven)
+    assert (got[3] == 0).all()
+    fails = check_against_oracle(uneven, got, idx=large[::3])
+    assert not fails, "\n".join(fails[:10])
+    t = bbs.bbs_var_default_tuning(1024)
+    for k in range(t.num_buckets):
+        t.wide[k] = 0
+    plan0 = bbs.VarPlan(handle, vbd, opts, t)
+    d0 = plan0.describe()
+    assert d0["wide_systems"] == 0 and d0["team_systems"] == d["team_systems"] + len(large)
+    got0 = run_plan(bbs, plan0, uneven)
+    assert np.array_equal(got0[3], got[3])
+    # BiCGSTAB without Jacobi and CG keep every team in the persistent launch
+    for kw in (dict(precond="none"), dict(solver="cg")):
+        assert bbs.VarPlan(handle, vbd, bbs.bbs_default_options(**kw)).describe()["wide_systems"] == 0
