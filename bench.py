@@ -62,15 +62,18 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 # scales them to its own launch of the same shape by systems (traffic is the
 # compulsory bytes, which grow in proportion). A kernel run on a workload
 # without a capture reports null, and an entry is removed when its kernel
-# changes. The uneven batch's entry is the capture of its first 20,000
-# systems; per-system bytes vary with n, so its scaling is approximate.
+# changes. The uneven batch's entries are captures of its first 20,000
+# systems (the persistent launch alone, and the graph of persistent, packed
+# and wide launches: the sum over its launches); per-system bytes vary with n,
+# so their scaling is approximate.
 TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (134.70e6, 16384),
            ("bicgstab_folded_kernel", "stencil2d5_12x12"): (280.75e6, 32768),
            ("cg_packed_kernel", "sym_stencil2d5_12x12_cg+jacobi"): (132.98e6, 16384),
            ("gmres_packed_kernel", "stencil2d5_12x12_gmres+jacobi"): (147.83e6, 16384),
            ("bicgstab_ilu_packed_kernel", "stencil2d5_12x12_bicgstab+ilu0"): (134.60e6, 16384),
-           ("refine_kernel", "stencil2d9_32x32"): (399.39e6, 4096),
-           ("varsize_kernel", "uneven_n16-1024"): (333.35e6, 20000)}
+           ("refine_kernel", "stencil2d9_32x32"): (400.29e6, 4096),
+           ("varsize_kernel", "uneven_n16-1024"): (333.35e6, 20000),
+           ("varsize_kernel+varpacked_kernel+varwide_kernel", "uneven_n16-1024"): (323.27e6, 20000)}
 
 
 # mixed refinement of the 32x32 9-point batch: the inner FP32 tolerance from a
@@ -121,6 +124,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="uneven workload: default launch choices")
+    p.add_argument("--tuning", default="", help="uneven workload: launch choices as JSON (an earlier line's "
+                   "iterations.tuning), instead of tuning")
     return p.parse_args()
 
 
@@ -323,7 +328,7 @@ class Uniform:
 class Uneven:
     """One graph launch of the persistent uneven-batch plan per step."""
 
-    def __init__(self, bbs, torch, dev, vb, tune=True):
+    def __init__(self, bbs, torch, dev, vb, tune=True, tuning=None):
         self.bbs, self.torch, self.dev, self.vb = bbs, torch, dev, vb
         self.label = vb.name
         self.vbd = bbs.VarDeviceBatch.from_varbatch(vb, dev)
@@ -333,8 +338,11 @@ class Uneven:
         self.h = bbs.Handle(dev.index or 0)
         self.opts = bbs.bbs_default_options()
         t0 = time.perf_counter()
-        self.tuning = (bbs.bbs_var_tune(self.h, self.vbd, self.b, self.x0, self.opts, sample=512)
-                       if tune else None)
+        if tuning is not None:  # a pinned tuning (the dict of an earlier run's line)
+            self.tuning = bbs.bbs_var_tuning.from_dict(tuning)
+        else:
+            self.tuning = (bbs.bbs_var_tune(self.h, self.vbd, self.b, self.x0, self.opts, sample=512)
+                           if tune else None)
         self.tune_s = time.perf_counter() - t0
         self.plan = bbs.VarPlan(self.h, self.vbd, self.opts, self.tuning)
         self.desc = self.plan.describe()
@@ -410,7 +418,7 @@ class Uneven:
 
 
 def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0, solver="bicgstab",
-                precond="jacobi", span=None, inner_tol=0.0):
+                precond="jacobi", span=None, inner_tol=0.0, tuning=None):
     if name == "mixed":
         wl = span_workload(subset_workload(W.mixed_precision(), systems), span)
         kw = dict(MIXED_OPTS)
@@ -427,7 +435,7 @@ def make_runner(name, bbs, torch, dev, systems=0, tune=True, fmt="csr", tps=0, s
         if span is not None:
             vb = vb.slice(*span)
             vb.name = vb.name.split("[")[0]
-        return Uneven(bbs, torch, dev, vb, tune=tune)
+        return Uneven(bbs, torch, dev, vb, tune=tune, tuning=tuning)
     wl = span_workload(subset_workload(W.plain_at_scale(symmetric=(solver == "cg")), systems), span)
     opts = {"threads_per_system": tps} if tps else {}
     opts.update(solver=solver, precond=precond)
@@ -865,7 +873,7 @@ def main():
     span = shard_span(args.workload, args.systems, rank, world) if args.shard else None
     r = make_runner(args.workload, bbs, torch, dev, args.systems, tune=not args.no_tune, fmt=args.format,
                     tps=args.threads_per_system, solver=args.solver, precond=args.precond, span=span,
-                    inner_tol=args.inner_tol)
+                    inner_tol=args.inner_tol, tuning=json.loads(args.tuning) if args.tuning else None)
     total_ms, solve_ms, clocks = time_steps(r, torch, stream, args.steps, args.warmup, dist,
                                             sample_clocks=True, dev_index=local)
     total_ms = max_over_ranks(total_ms, dist, dev)  # the job's time is its slowest rank's

@@ -196,10 +196,19 @@ __device__ __forceinline__ void refine_system(const SolveParams& P, const SysIO&
                                               float* xa, float* xb, const Team& tm) {
     const int n = P.n;
     int par64 = 0, par32 = 0;
-    double b[R], x[R], r[R];
+    // b is re-read from memory for each residual rather than held in
+    // registers through the inner solves (which need every register)
+    double x[R], r[R];
     float w[R], d[R];
-    load_system<R>(io, b, x, tm);
-    double s0[1] = {pdot(b, b)};
+    double bb = 0.0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        const double bq = row < n ? io.b[row] : 0.0;
+        x[q] = row < n ? io.x[row] : 0.0;
+        bb = fma(bq, bq, bb);
+    }
+    double s0[1] = {bb};
     block_sum(s0, red64, par64, tm);
     const double nb2 = s0[0];
     if (!finite(nb2)) {
@@ -216,7 +225,20 @@ __device__ __forceinline__ void refine_system(const SolveParams& P, const SysIO&
     int status = -1, k = 0, inner_total = 0;
     double rr = 0.0;
     for (k = 0;; ++k) {
-        rr = true_residual(op64, b, x, r, xd, red64, par64, tm, n);
+        {  // r = b - A x in FP64
+            put(xd, x, tm, n);
+            tm.sync();
+            double ax[R];
+            op64.apply(xd, ax, tm);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int row = tm.row(q);
+                r[q] = (row < n ? io.b[row] : 0.0) - ax[q];
+            }
+            double s1[1] = {pdot(r, r)};
+            block_sum(s1, red64, par64, tm);
+            rr = s1[0];
+        }
         if (!finite(rr)) { status = ST_NAN; break; }
         if (rr <= tau2) { status = ST_CONVERGED; break; }
         if (k >= P.max_outer) { status = ST_MAX_ITER; break; }
