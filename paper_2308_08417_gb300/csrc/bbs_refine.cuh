@@ -196,29 +196,36 @@ __device__ __forceinline__ void refine_system(const SolveParams& P, const SysIO&
                                               float* xa, float* xb, const Team& tm) {
     const int n = P.n;
     int par64 = 0, par32 = 0;
-    // b is re-read from memory for each residual rather than held in
-    // registers through the inner solves (which need every register)
-    double x[R], r[R];
+    // Neither b nor x is held in registers through the inner solves (which
+    // need every register): b is re-read from memory for each residual, and
+    // x lives in xd, the shared FP64 vector the residual's SpMV reads (each
+    // thread updates its own rows).
+    double r[R];
     float w[R], d[R];
     double bb = 0.0;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int row = tm.row(q);
-        const double bq = row < n ? io.b[row] : 0.0;
-        x[q] = row < n ? io.x[row] : 0.0;
-        bb = fma(bq, bq, bb);
+        if (row < n) {
+            const double bq = io.b[row];
+            xd[row] = io.x[row];
+            bb = fma(bq, bq, bb);
+        }
     }
     double s0[1] = {bb};
     block_sum(s0, red64, par64, tm);
     const double nb2 = s0[0];
-    if (!finite(nb2)) {
-        write_result(io, x, ST_NAN, 0, quiet_nan(), 0, tm);
-        return;
-    }
-    if (nb2 == 0.0) {
+    if (!finite(nb2) || nb2 == 0.0) {  // x stays x0, or x = 0
+        double x[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = 0.0;
-        write_result(io, x, ST_CONVERGED, 0, 0.0, 0, tm);
+        for (int q = 0; q < R; ++q) {
+            const int row = tm.row(q);
+            x[q] = (nb2 == 0.0 || row >= n) ? 0.0 : xd[row];
+        }
+        if (nb2 == 0.0)
+            write_result(io, x, ST_CONVERGED, 0, 0.0, 0, tm);
+        else
+            write_result(io, x, ST_NAN, 0, quiet_nan(), 0, tm);
         return;
     }
     const double tau2 = (P.tol_type == 1) ? P.tol * P.tol * nb2 : P.tol * P.tol;
@@ -226,7 +233,6 @@ __device__ __forceinline__ void refine_system(const SolveParams& P, const SysIO&
     double rr = 0.0;
     for (k = 0;; ++k) {
         {  // r = b - A x in FP64
-            put(xd, x, tm, n);
             tm.sync();
             double ax[R];
             op64.apply(xd, ax, tm);
@@ -248,8 +254,18 @@ __device__ __forceinline__ void refine_system(const SolveParams& P, const SysIO&
         for (int q = 0; q < R; ++q) w[q] = (float)(r[q] * rinv);
         inner_total += inner_bicgstab32<R>(op32, dinv, w, d, (float)P.inner_tol, P.max_iters, xa, xb, red32,
                                            par32, tm, n);
+        tm.sync();  // every thread is done reading xd (the inner solve has no FP64 reads of it)
 #pragma unroll
-        for (int q = 0; q < R; ++q) x[q] = fma(rn, (double)d[q], x[q]);
+        for (int q = 0; q < R; ++q) {
+            const int row = tm.row(q);
+            if (row < n) xd[row] = fma(rn, (double)d[q], xd[row]);
+        }
+    }
+    double x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int row = tm.row(q);
+        x[q] = row < n ? xd[row] : 0.0;
     }
     write_result(io, x, status, k, sqrt(rr / nb2), inner_total, tm);
 }
