@@ -84,6 +84,11 @@ __device__ __forceinline__ bool finite64(double v) {
     return (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
 }
 __device__ __forceinline__ bool zero64(double v) { return (__double_as_longlong(v) << 1) == 0; }
+// Neither zero, subnormal, infinite nor NaN (its exponent field is neither 0 nor all ones).
+__device__ __forceinline__ bool normal64(double v) {
+    const long long e = __double_as_longlong(v) & 0x7ff0000000000000LL;
+    return e != 0 && e != 0x7ff0000000000000LL;
+}
 __device__ __forceinline__ bool le_nonneg64(double a, double b) {
     return __double_as_longlong(a) <= __double_as_longlong(b);
 }

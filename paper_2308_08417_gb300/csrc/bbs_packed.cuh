@@ -132,7 +132,11 @@ __device__ __forceinline__ void bicgstab_packed_system(const PackedOp<FMT, R>& o
             have_res = false;
         }
     }
-    double rho = rr, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    // beta = (rho alpha) / (rho_old omega): cfac holds alpha / (rho omega) of
+    // the previous step, found with omega = ts / tt from one division (1
+    // before the first step and after a restart, where p = 0 and v = 0 make
+    // beta irrelevant)
+    double rho = rr, alpha = 1.0, omega = 1.0, cfac = 1.0;
     __syncwarp();  // every lane is done reading xa
 #pragma unroll
     for (int q = 0; q < R; ++q) {
@@ -153,7 +157,7 @@ __device__ __forceinline__ void bicgstab_packed_system(const PackedOp<FMT, R>& o
                 active = false;
             }
         }
-        const double beta = (rho * alpha) / (rho_old * omega);
+        const double beta = rho * cfac;
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int row = tm.row(q);
@@ -203,8 +207,22 @@ __device__ __forceinline__ void bicgstab_packed_system(const PackedOp<FMT, R>& o
                 active = false;
                 full = false;
             }
-            const double om = zero64(tt) ? 0.0 : ts / tt;
-            if (full) omega = om;
+            // omega = ts / tt and the next beta's alpha / (rho omega) =
+            // alpha tt / (rho ts) from one division; plain divisions where the
+            // product is not a normal number
+            const double den = tt * rho * ts;
+            const double inv = 1.0 / den;
+            double om = (ts * inv) * (rho * ts);
+            double cf = (tt * inv) * (alpha * tt);
+            const bool fast = normal64(den) && finite64(om) && finite64(cf);
+            if (__any_sync(kFull, !fast) && !fast) {
+                om = zero64(tt) ? 0.0 : ts / tt;
+                cf = (alpha * tt) / (rho * ts);
+            }
+            if (full) {
+                omega = om;
+                cfac = cf;
+            }
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int row = tm.row(q);
@@ -251,7 +269,7 @@ __device__ __forceinline__ void bicgstab_packed_system(const PackedOp<FMT, R>& o
                         if (row < n) sm.xa[row] = 0.0;
                     }
                     rho = res2;
-                    rho_old = alpha = omega = 1.0;
+                    alpha = omega = cfac = 1.0;
                     restarted = true;
                 }
             }
@@ -261,7 +279,6 @@ __device__ __forceinline__ void bicgstab_packed_system(const PackedOp<FMT, R>& o
                 status = ST_BREAKDOWN;
                 active = false;
             } else {
-                rho_old = rho;
                 rho = rho_next;
             }
         }
@@ -385,7 +402,17 @@ __device__ __forceinline__ void cg_packed_system(const PackedOp<FMT, R>& op, con
                 active = false;
             }
         }
-        const double alpha = rho / pt;
+        // alpha = rho / pt and 1 / rho (for the ratio below) from one division;
+        // plain divisions where the product is not a normal number
+        const double den = pt * rho;
+        const double inv = 1.0 / den;
+        double alpha = (rho * inv) * rho;
+        double rinv = pt * inv;
+        const bool fast = normal64(den) && finite64(alpha) && finite64(rinv);
+        if (__any_sync(kFull, !fast) && !fast) {
+            alpha = rho / pt;
+            rinv = 1.0 / rho;
+        }
         double s2[2] = {0.0, 0.0};
 #pragma unroll
         for (int q = 0; q < R; ++q) {
@@ -409,7 +436,7 @@ __device__ __forceinline__ void cg_packed_system(const PackedOp<FMT, R>& op, con
         }
         // p = z + (rho_new / rho) p now, before a confirmation may reuse t;
         // a restart below replaces p with M r_true.
-        const double ratio = s2[1] / rho;
+        const double ratio = s2[1] * rinv;
 #pragma unroll
         for (int q = 0; q < R; ++q) p[q] = fma(ratio, p[q], t[q]);
         bool restarted = false;
@@ -449,7 +476,9 @@ __device__ __forceinline__ void cg_packed_system(const PackedOp<FMT, R>& op, con
                 }
             }
         }
-        if (!restarted && active) rho = s2[1];
+        // (unconditional: a stopped system's rho is never read again, and the
+        // old rho is then dead once 1 / rho is known)
+        if (!restarted) rho = s2[1];
     }
     if (active) status = ST_MAX_ITER;
     const bool need = valid && special == 0 && !have_res;
