@@ -159,6 +159,22 @@ __device__ __forceinline__ Op<FMT, R, double, double> make_op(const SolveParams&
 
 // ------------------------------------------------------------- BiCGSTAB
 
+// omega = ts / tt and alpha / (rho omega) = alpha tt / (rho ts), the factor
+// of the next beta = (rho' alpha) / (rho omega), from one division (one
+// reciprocal of tt rho ts); plain divisions where that product or a result is
+// not a normal number. omega = 0 for tt = 0.
+__device__ __forceinline__ void omega_and_cfac(double tt, double ts, double rho, double alpha, double& omega,
+                                               double& cfac) {
+    const double den = tt * rho * ts;
+    const double inv = 1.0 / den;
+    omega = (ts * inv) * (rho * ts);
+    cfac = (tt * inv) * (alpha * tt);
+    if (!(normal64(den) && finite64(omega) && finite64(cfac))) {
+        omega = zero64(tt) ? 0.0 : ts / tt;
+        cfac = (alpha * tt) / (rho * ts);
+    }
+}
+
 // Right-preconditioned BiCGSTAB (van der Vorst), M = D^-1, per system:
 //   rho = r^.r ; beta = (rho alpha)/(rho_old omega) ; p = r + beta (p - omega v)
 //   p^ = M p ; v = A p^ ; alpha = rho / r^.v ; s = r - alpha v
@@ -207,7 +223,7 @@ __device__ __forceinline__ void bicgstab_system(const Op<FMT, R, double, double>
         status = ST_CONVERGED;
     } else {
         double rho = rr;  // r^ = r, so r^.r = ||r||^2
-        double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        double alpha = 1.0, omega = 1.0, cfac = 1.0;  // cfac: as in bicgstab_scaled_system
         int restarts = 0;
 #pragma unroll
         for (int q = 0; q < R; ++q) {
@@ -220,7 +236,7 @@ __device__ __forceinline__ void bicgstab_system(const Op<FMT, R, double, double>
             iters = it;
             if (!finite(rho)) { status = ST_NAN; break; }
             if (rho == 0.0) { status = ST_BREAKDOWN; break; }
-            const double beta = (rho * alpha) / (rho_old * omega);
+            const double beta = rho * cfac;
 #pragma unroll
             for (int q = 0; q < R; ++q) p[q] = fma(beta, fma(-omega, v[q], p[q]), r[q]);
             {
@@ -262,7 +278,7 @@ __device__ __forceinline__ void bicgstab_system(const Op<FMT, R, double, double>
                 candidate = true;
             } else {
                 if (!finite(tt) || !finite(ts)) { status = ST_NAN; break; }
-                omega = (tt == 0.0) ? 0.0 : ts / tt;
+                omega_and_cfac(tt, ts, rho, alpha, omega, cfac);
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     const int row = tm.row(q);
@@ -290,11 +306,10 @@ __device__ __forceinline__ void bicgstab_system(const Op<FMT, R, double, double>
                     v[q] = 0.0;
                 }
                 rho = res2;
-                rho_old = alpha = omega = 1.0;
+                alpha = omega = cfac = 1.0;
                 continue;
             }
             if (omega == 0.0) { status = ST_BREAKDOWN; break; }
-            rho_old = rho;
             rho = rho_next;
         }
         if (status < 0) status = ST_MAX_ITER;
@@ -415,7 +430,9 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
     } else if (le_nonneg64(rr, tau2)) {
         status = ST_CONVERGED;
     } else {
-        double rho = rr, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        // beta = (rho alpha) / (rho_old omega): cfac holds alpha / (rho omega)
+        // of the previous step, found with omega from one division
+        double rho = rr, alpha = 1.0, omega = 1.0, cfac = 1.0;
         int restarts = 0;
 #pragma unroll
         for (int q = 0; q < R; ++q) {
@@ -428,7 +445,7 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
             iters = it;
             if (!finite64(rho)) { status = ST_NAN; break; }
             if (zero64(rho)) { status = ST_BREAKDOWN; break; }
-            const double beta = (rho * alpha) / (rho_old * omega);
+            const double beta = rho * cfac;
 #pragma unroll
             for (int q = 0; q < R; ++q) p[q] = fma(beta, fma(-omega, v[q], p[q]), r[q]);
             put(sm.xa, p, tm, n);
@@ -457,7 +474,7 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
                 candidate = true;
             } else {
                 if (!finite64(tt) || !finite64(ts)) { status = ST_NAN; break; }
-                omega = zero64(tt) ? 0.0 : ts / tt;
+                omega_and_cfac(tt, ts, rho, alpha, omega, cfac);
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     xs[q] = fma(omega, r[q], fma(alpha, p[q], xs[q]));
@@ -484,11 +501,10 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
                     v[q] = 0.0;
                 }
                 rho = res2;
-                rho_old = alpha = omega = 1.0;
+                alpha = omega = cfac = 1.0;
                 continue;
             }
             if (zero64(omega)) { status = ST_BREAKDOWN; break; }
-            rho_old = rho;
             rho = rho_next;
         }
         if (status < 0) status = ST_MAX_ITER;
