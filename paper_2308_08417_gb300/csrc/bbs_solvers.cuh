@@ -380,7 +380,9 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
                                                        const TeamSmem& sm, const Team& tm) {
     const int n = io.n;
     int parity = 0;
-    double xs[R], r[R], rh[R], p[R], v[R], t[R];
+    // p lives in shared memory only (xa, the SpMV input it is copied to
+    // anyway), which leaves five register vectors
+    double xs[R], r[R], rh[R], v[R], t[R];
     {
         double dinv[R];
         jacobi_setup<FMT, R>(op.A, true, dinv, tm);
@@ -434,11 +436,13 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
         // of the previous step, found with omega from one division
         double rho = rr, alpha = 1.0, omega = 1.0, cfac = 1.0;
         int restarts = 0;
+        tm.sync();  // every thread is done reading xa (the residual's SpMV input)
 #pragma unroll
         for (int q = 0; q < R; ++q) {
+            const int row = tm.row(q);
             rh[q] = r[q];
-            p[q] = 0.0;
             v[q] = 0.0;
+            if (row < n) sm.xa[row] = 0.0;  // p = 0
         }
         have_res = false;
         for (int it = 1; it <= C.max_iters; ++it) {
@@ -447,8 +451,10 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
             if (zero64(rho)) { status = ST_BREAKDOWN; break; }
             const double beta = rho * cfac;
 #pragma unroll
-            for (int q = 0; q < R; ++q) p[q] = fma(beta, fma(-omega, v[q], p[q]), r[q]);
-            put(sm.xa, p, tm, n);
+            for (int q = 0; q < R; ++q) {
+                const int row = tm.row(q);
+                if (row < n) sm.xa[row] = fma(beta, fma(-omega, v[q], sm.xa[row]), r[q]);
+            }
             tm.sync();
             op.apply(sm.xa, v, tm);
             double s1[1] = {pdot(rh, v)};
@@ -470,14 +476,18 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
             double rho_next = 0.0;
             if (le_nonneg64(ss, tau2)) {
 #pragma unroll
-                for (int q = 0; q < R; ++q) xs[q] = fma(alpha, p[q], xs[q]);
+                for (int q = 0; q < R; ++q) {
+                    const int row = tm.row(q);
+                    xs[q] = fma(alpha, row < n ? sm.xa[row] : 0.0, xs[q]);
+                }
                 candidate = true;
             } else {
                 if (!finite64(tt) || !finite64(ts)) { status = ST_NAN; break; }
                 omega_and_cfac(tt, ts, rho, alpha, omega, cfac);
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    xs[q] = fma(omega, r[q], fma(alpha, p[q], xs[q]));
+                    const int row = tm.row(q);
+                    xs[q] = fma(omega, r[q], fma(alpha, row < n ? sm.xa[row] : 0.0, xs[q]));
                     r[q] = fma(-omega, t[q], r[q]);
                 }
                 double s2[2] = {pdot(r, r), pdot(rh, r)};
@@ -494,11 +504,13 @@ __device__ __forceinline__ void bicgstab_scaled_system(const Op<FMT, R, double, 
                 if (le_nonneg64(res2, tau2)) { status = ST_CONVERGED; break; }
                 if (++restarts > kMaxRestarts) { status = ST_MAX_ITER; break; }
                 have_res = false;
+                tm.sync();  // every thread is done reading xa (the residual's SpMV input)
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
+                    const int row = tm.row(q);
                     rh[q] = r[q];
-                    p[q] = 0.0;
                     v[q] = 0.0;
+                    if (row < n) sm.xa[row] = 0.0;  // p = 0
                 }
                 rho = res2;
                 alpha = omega = cfac = 1.0;
