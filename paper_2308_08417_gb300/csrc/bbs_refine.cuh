@@ -122,15 +122,24 @@ __device__ __forceinline__ void stage_values_rounded(const double* __restrict__ 
 //
 // With the width compiled in (K > 0, always odd: 3-, 5-, 7- and 9-point
 // rows), the first K - 1 slots of each of a thread's rows are stored in
-// pairs: slots 2i and 2i + 1 side by side, so that one 8-byte load brings
-// both values and one 4-byte load both columns; the row's last slot follows
-// all the pairs, alone. Same bytes, a third fewer shared-memory loads in the
-// SpMV, and the same order of accumulation.
+// groups side by side: quads of slots 4i..4i + 3 (one 16-byte load brings
+// their values, one 8-byte load their columns), then a pair when K - 1 is not
+// a multiple of 4 (8- and 4-byte loads), then the row's last slot alone.
+// Same bytes, fewer shared-memory loads in the SpMV (for K = 9: 15 per row
+// instead of 27), and the same order of accumulation.
+template <int K>
+struct SlotGroups {
+    static_assert(K % 2 == 1, "the grouped layout is for odd ELL widths");
+    static constexpr int NQ = (K - 1) / 4;        // quads per row
+    static constexpr int NP = ((K - 1) % 4) / 2;  // pairs per row (0 or 1)
+};
+
 template <int R, int K>
 __device__ __forceinline__ int paired_slot(int q, int j, int nt, int tid) {
-    static_assert(K % 2 == 1, "the paired layout is for odd ELL widths");
-    constexpr int KP = (K - 1) / 2;
-    return j < 2 * KP ? ((q * KP + (j >> 1)) * nt + tid) * 2 + (j & 1) : 2 * R * KP * nt + q * nt + tid;
+    constexpr int NQ = SlotGroups<K>::NQ, NP = SlotGroups<K>::NP;
+    if (j < 4 * NQ) return ((q * NQ + (j >> 2)) * nt + tid) * 4 + (j & 3);
+    if (j < 4 * NQ + 2 * NP) return 4 * R * NQ * nt + (q * nt + tid) * 2 + ((j - 4 * NQ) & 1);
+    return (4 * NQ + 2 * NP) * R * nt + q * nt + tid;
 }
 
 template <int R, int K = 0>
@@ -177,20 +186,34 @@ struct PairOp32 {
         const int kk = K > 0 ? K : k;
         const uint16_t* cl = reinterpret_cast<const uint16_t*>(vals + (size_t)R * kk * tm.nt);
         const int nt = tm.nt;
-        if constexpr (K > 0) {  // the paired layout of stage_pairs_ell
-            constexpr int KP = (K - 1) / 2;
-            const float2* v2 = reinterpret_cast<const float2*>(vals);
-            const uint32_t* c2 = reinterpret_cast<const uint32_t*>(cl);
-            const float* v1 = vals + 2 * R * KP * nt;
-            const uint16_t* c1 = cl + 2 * R * KP * nt;
+        if constexpr (K > 0) {  // the grouped layout of stage_pairs_ell
+            constexpr int NQ = SlotGroups<K>::NQ, NP = SlotGroups<K>::NP;
+            const float4* v4 = reinterpret_cast<const float4*>(vals);
+            const uint2* c4 = reinterpret_cast<const uint2*>(cl);
+            const float2* v2 = reinterpret_cast<const float2*>(vals + 4 * R * NQ * nt);
+            const uint32_t* c2 = reinterpret_cast<const uint32_t*>(cl + 4 * R * NQ * nt);
+            const float* v1 = vals + (4 * NQ + 2 * NP) * R * nt;
+            const uint16_t* c1 = cl + (4 * NQ + 2 * NP) * R * nt;
             float sum[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) sum[q] = 0.0f;
 #pragma unroll
-            for (int pj = 0; pj < KP; ++pj) {
+            for (int g = 0; g < NQ; ++g) {
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    const int o = (q * KP + pj) * nt + tm.tid;
+                    const int o = (q * NQ + g) * nt + tm.tid;
+                    const float4 a = v4[o];
+                    const uint2 cc = c4[o];
+                    sum[q] = fmaf(a.x, xs[cc.x & 0xffffu], sum[q]);
+                    sum[q] = fmaf(a.y, xs[cc.x >> 16], sum[q]);
+                    sum[q] = fmaf(a.z, xs[cc.y & 0xffffu], sum[q]);
+                    sum[q] = fmaf(a.w, xs[cc.y >> 16], sum[q]);
+                }
+            }
+            if constexpr (NP > 0) {
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int o = q * nt + tm.tid;
                     const float2 a = v2[o];
                     const uint32_t cc = c2[o];
                     sum[q] = fmaf(a.x, xs[cc & 0xffffu], sum[q]);
