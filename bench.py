@@ -71,7 +71,7 @@ TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (135.12e6, 16384),
            ("cg_packed_kernel", "sym_stencil2d5_12x12_cg+jacobi"): (133.40e6, 16384),
            ("gmres_packed_kernel", "stencil2d5_12x12_gmres+jacobi"): (147.83e6, 16384),
            ("bicgstab_ilu_packed_kernel", "stencil2d5_12x12_bicgstab+ilu0"): (134.60e6, 16384),
-           ("refine_kernel", "stencil2d9_32x32"): (397.56e6, 4096),
+           ("refine_kernel", "stencil2d9_32x32"): (396.44e6, 4096),
            ("varsize_kernel", "uneven_n16-1024"): (333.46e6, 20000),
            ("varsize_kernel+varpacked_kernel+varwide_kernel", "uneven_n16-1024"): (323.15e6, 20000)}
 
