@@ -378,8 +378,10 @@ bbs_status bbs_var_plan_destroy(bbs_var_plan *plan);
  * kernel on a sample of the bucket's systems (at least `sample`, and at least
  * four times the systems the GPU holds at once, so that each trial measures
  * throughput; all of them when the bucket is smaller) for each team
- * size and staging choice (and both block shapes), and write the fastest
- * choices to *tuning. b and x0 are DEVICE arrays of the batch; x0 is not
+ * size and staging choice (and both block shapes), then packing and wide
+ * teams where the bucket has such systems, and write the fastest choices to
+ * *tuning (packing and wide teams keep the default tuning's choice unless the
+ * other one times at least 1 % faster). b and x0 are DEVICE arrays of the batch; x0 is not
  * modified (trials run on a private copy). Synchronous; allocates and frees
  * its own scratch. */
 bbs_status bbs_var_tune(bbs_handle *handle, const bbs_var_batch *batch,

@@ -805,7 +805,7 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
         if (build_plan(h, in, &pl) != BBS_OK) return INFINITY;
         float ms_sum = 0.f;
         bool ok = true;
-        for (int rep = 0; rep < 3 && ok; ++rep) {
+        for (int rep = 0; rep < 4 && ok; ++rep) {
             cudaMemcpyAsync(dx, x0, sizeof(double) * vec_len, cudaMemcpyDeviceToDevice, st);
             cudaEventRecord(e0, st);
             ok = bbs_var_solve(pl, b, dx, &lg, st) == BBS_OK;
@@ -816,7 +816,7 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
             if (rep > 0) ms_sum += ms;
         }
         bbs_var_plan_destroy(pl);
-        return ok ? ms_sum / 2.0 / samp[k].size() : INFINITY;
+        return ok ? ms_sum / 3.0 / samp[k].size() : INFINITY;
     };
 
     bbs_var_tuning best_overall = base;
@@ -846,20 +846,26 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
                         bests = stg;
                     }
                 }
-            // packing the bucket's small systems, the rest as the best team choice
+            // Packing the bucket's small systems (the rest as the best team
+            // choice), then wide teams for its systems that need more than 8
+            // rows per thread on their fewest warps. Each is kept or dropped
+            // against the default tuning's choice, which the trial must beat
+            // by 1 % to be overturned: near-equal trials then give the same
+            // plan from run to run.
+            const auto prefer = [](double alt, double cur, bool alt_is_default) {
+                return alt_is_default ? alt <= cur * 1.01 : alt < cur * 0.99;
+            };
             if (nmin <= kVarPackMaxN) {
                 const double per = trial(k, bw, bestw, bests, 1, 0);
-                if (per < best) {
+                if (prefer(per, best, base.pack[k] != 0)) {
                     best = per;
                     bestp = 1;
                 }
             }
-            // wide teams for the bucket's systems that need more than 8 rows per
-            // thread on their fewest warps
             int bestwide = 0;
             if (o->solver == BBS_SOLVER_BICGSTAB && o->precond == BBS_PREC_JACOBI && nk > 32 * 8) {
                 const double per = trial(k, bw, bestw, bests, bestp, 1);
-                if (per < best) {
+                if (prefer(per, best, base.wide[k] != 0)) {
                     best = per;
                     bestwide = 1;
                 }
