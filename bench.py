@@ -73,6 +73,7 @@ TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (135.12e6, 16384),
            ("bicgstab_ilu_packed_kernel", "stencil2d5_12x12_bicgstab+ilu0"): (134.60e6, 16384),
            ("refine_kernel", "stencil2d9_32x32"): (396.44e6, 4096),
            ("varsize_kernel", "uneven_n16-1024"): (333.46e6, 20000),
+           ("varsize_kernel+varpacked_kernel", "uneven_n16-1024"): (336.08e6, 20000),
            ("varsize_kernel+varpacked_kernel+varwide_kernel", "uneven_n16-1024"): (323.15e6, 20000)}
 
 
