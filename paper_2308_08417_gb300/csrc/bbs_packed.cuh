@@ -208,16 +208,18 @@ __device__ __forceinline__ void bicgstab_packed_system(const PackedOp<FMT, R>& o
                 full = false;
             }
             // omega = ts / tt and the next beta's alpha / (rho omega) =
-            // alpha tt / (rho ts) from one division; plain divisions where the
-            // product is not a normal number
+            // alpha tt / (rho ts) from one division; where the product or a
+            // quotient leaves the normal range (systems scaled far from 1),
+            // plain divisions in the original form
             const double den = tt * rho * ts;
             const double inv = 1.0 / den;
-            double om = (ts * inv) * (rho * ts);
-            double cf = (tt * inv) * (alpha * tt);
-            const bool fast = normal64(den) && finite64(om) && finite64(cf);
+            const double qs = ts * inv, qt = tt * inv;  // 1 / (tt rho), 1 / (rho ts)
+            double om = qs * (rho * ts);
+            double cf = qt * (alpha * tt);
+            const bool fast = normal64(den) && normal64(qs) && normal64(qt) && finite64(om) && finite64(cf);
             if (__any_sync(kFull, !fast) && !fast) {
                 om = zero64(tt) ? 0.0 : ts / tt;
-                cf = (alpha * tt) / (rho * ts);
+                cf = alpha / (rho * om);
             }
             if (full) {
                 omega = om;
@@ -406,9 +408,10 @@ __device__ __forceinline__ void cg_packed_system(const PackedOp<FMT, R>& op, con
         // plain divisions where the product is not a normal number
         const double den = pt * rho;
         const double inv = 1.0 / den;
-        double alpha = (rho * inv) * rho;
+        const double qp = rho * inv;  // 1 / pt
+        double alpha = qp * rho;
         double rinv = pt * inv;
-        const bool fast = normal64(den) && finite64(alpha) && finite64(rinv);
+        const bool fast = normal64(den) && normal64(qp) && normal64(rinv) && finite64(alpha);
         if (__any_sync(kFull, !fast) && !fast) {
             alpha = rho / pt;
             rinv = 1.0 / rho;

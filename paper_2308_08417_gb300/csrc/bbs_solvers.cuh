@@ -161,17 +161,19 @@ __device__ __forceinline__ Op<FMT, R, double, double> make_op(const SolveParams&
 
 // omega = ts / tt and alpha / (rho omega) = alpha tt / (rho ts), the factor
 // of the next beta = (rho' alpha) / (rho omega), from one division (one
-// reciprocal of tt rho ts); plain divisions where that product or a result is
-// not a normal number. omega = 0 for tt = 0.
+// reciprocal of tt rho ts); where that product or a quotient leaves the
+// normal range (systems scaled far from 1), plain divisions in the original
+// form. omega = 0 for tt = 0.
 __device__ __forceinline__ void omega_and_cfac(double tt, double ts, double rho, double alpha, double& omega,
                                                double& cfac) {
     const double den = tt * rho * ts;
     const double inv = 1.0 / den;
-    omega = (ts * inv) * (rho * ts);
-    cfac = (tt * inv) * (alpha * tt);
-    if (!(normal64(den) && finite64(omega) && finite64(cfac))) {
+    const double qs = ts * inv, qt = tt * inv;  // 1 / (tt rho), 1 / (rho ts)
+    omega = qs * (rho * ts);
+    cfac = qt * (alpha * tt);
+    if (!(normal64(den) && normal64(qs) && normal64(qt) && finite64(omega) && finite64(cfac))) {
         omega = zero64(tt) ? 0.0 : ts / tt;
-        cfac = (alpha * tt) / (rho * ts);
+        cfac = alpha / (rho * omega);
     }
 }
 

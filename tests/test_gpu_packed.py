@@ -356,3 +356,27 @@ def test_host_buffer_chunks_match_the_device_solve(bbs, handle):
     assert np.array_equal(hx.numpy(), dev[0])
     assert np.array_equal(log.iters.numpy(), dev[1]) and np.array_equal(log.status.numpy(), dev[3])
     assert np.array_equal(log.rel_res.numpy(), dev[2])
+
+
+@pytest.mark.parametrize("exp", [300, -300])
+def test_extreme_scales_take_the_plain_divisions(bbs, handle, exp):
+    """b scaled by 2^exp: every iterate scales exactly, but (t, t) rho (t, s)
+    overflows or underflows, so omega and the next beta fall back to plain
+    divisions. The packed BiCGSTAB and CG and the one-system-per-warp
+    BiCGSTAB still meet the oracle bar on the scaled batch and take the
+    iterations of the unscaled one (within the bar)."""
+    scale = 2.0 ** exp
+    for solver, symmetric in (("bicgstab", False), ("cg", True)):
+        wl = W.plain_at_scale(97, symmetric=symmetric)
+        A = wl.matrix("csr")
+        b = wl.b * scale
+        r = oracle.solve_batch(A, b, solver=solver)
+        r1 = oracle.solve_batch(A, wl.b, solver=solver)
+        assert np.array_equal(r[1], r1[1])  # the oracle's iterates scale exactly
+        for tps in (0, 32):
+            g = gpu_solve(bbs, handle, A, b, solver=solver, threads_per_system=tps)
+            fails = compare(*g[:4], r[0], r[1], r[3], rel_host=host_rel_residual(dense_of(wl), g[0], b),
+                            label=f"{solver} tps={tps} 2^{exp}")
+            assert not fails, "\n".join(fails)
+            g1 = gpu_solve(bbs, handle, A, wl.b, solver=solver, threads_per_system=tps)
+            assert np.abs(g[1].astype(int) - g1[1].astype(int)).max() <= 2
