@@ -66,15 +66,15 @@ HBM_GBS = 6789.0  # measured copy bandwidth of the GB300s
 # systems (the persistent launch alone, and the graph of persistent, packed
 # and wide launches: the sum over its launches); per-system bytes vary with n,
 # so their scaling is approximate.
-TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (135.12e6, 16384),
-           ("bicgstab_folded_kernel", "stencil2d5_12x12"): (280.12e6, 32768),
-           ("cg_packed_kernel", "sym_stencil2d5_12x12_cg+jacobi"): (133.40e6, 16384),
+TRAFFIC = {("bicgstab_packed_kernel", "stencil2d5_12x12"): (135.11e6, 16384),
+           ("bicgstab_folded_kernel", "stencil2d5_12x12"): (280.72e6, 32768),
+           ("cg_packed_kernel", "sym_stencil2d5_12x12_cg+jacobi"): (133.00e6, 16384),
            ("gmres_packed_kernel", "stencil2d5_12x12_gmres+jacobi"): (147.83e6, 16384),
            ("bicgstab_ilu_packed_kernel", "stencil2d5_12x12_bicgstab+ilu0"): (134.60e6, 16384),
            ("refine_kernel", "stencil2d9_32x32"): (396.44e6, 4096),
-           ("varsize_kernel", "uneven_n16-1024"): (333.39e6, 20000),
-           ("varsize_kernel+varpacked_kernel", "uneven_n16-1024"): (336.08e6, 20000),
-           ("varsize_kernel+varpacked_kernel+varwide_kernel", "uneven_n16-1024"): (323.46e6, 20000)}
+           ("varsize_kernel", "uneven_n16-1024"): (333.05e6, 20000),
+           ("varsize_kernel+varpacked_kernel", "uneven_n16-1024"): (336.46e6, 20000),
+           ("varsize_kernel+varpacked_kernel+varwide_kernel", "uneven_n16-1024"): (323.93e6, 20000)}
 
 
 # mixed refinement of the 32x32 9-point batch: the inner FP32 tolerance from a
