@@ -26,7 +26,8 @@ def nvcc() -> str:
 
 
 # Translation units that take longest to compile start first.
-_SLOW_FIRST = ("bbs_varsize_k8", "bbs_varsize_k4", "bbs_k_bicgstab_", "bbs_k_gmres_", "bbs_k_cg_")
+_SLOW_FIRST = ("bbs_varwide_hi", "bbs_varsize_k8", "bbs_varwide_lo", "bbs_varsize_k4", "bbs_k_bicgstab_",
+               "bbs_varpacked_", "bbs_k_gmres_", "bbs_k_cg_")
 
 
 def sources():
