@@ -307,12 +307,14 @@ typedef struct {
  * whether its small systems are packed (pack[b] = 1: a system of at most 160
  * rows whose group fits shared memory is solved by 4, 8 or 16 lanes, with
  * 8, 4 or 2 systems per warp in lockstep, as bbs_solve packs uniform batches;
- * 0: one team per system), and whether its large systems run as wide teams
- * (wide[b] = 1, BiCGSTAB with Jacobi only: a system that needs more than 8
- * rows per thread on the fewest warps that hold it in at most 16 rows per
- * thread (1, 2 or 4 warps) is solved by that many warps, one block per system,
- * values staged, in a launch of its own, where such blocks still leave an SM
- * 8 warps; 0: every team runs in the persistent launch). block_warps is 8 (up to 8 rows per thread) or 16 (up to 4 rows per
+ * 0: one team per system), and which of its large systems run as wide teams
+ * (wide[b], BiCGSTAB with Jacobi only, a bit set: 1 = systems whose rows hold
+ * at most 4 stored values on average, 2 = the others, 3 = both, 0 = none. Such
+ * a system, if it needs more than 8 rows per thread on the fewest warps that
+ * hold it in at most 16 rows per thread (1, 2 or 4 warps), is solved by that
+ * many warps, one block per system, values staged, in a launch of its own,
+ * where such blocks still leave an SM 8 warps; the others run in the
+ * persistent launch). block_warps is 8 (up to 8 rows per thread) or 16 (up to 4 rows per
  * thread). The planner lowers a bucket's warps to those of the next larger
  * bucket if they exceed them and raises them to the minimum its rows need. */
 typedef struct {
@@ -330,7 +332,8 @@ typedef struct bbs_var_plan bbs_var_plan;
 
 /* Default tuning: power-of-two buckets up to max_n, one warp per 5 rows per
  * thread (as bbs_default_block_size), values streamed, small systems packed,
- * wide teams in the buckets above 512 rows, 8-warp blocks. Host only. */
+ * wide teams for the sparse rows (wide = 1) of the buckets above 512 rows,
+ * 8-warp blocks. Host only. */
 bbs_status bbs_var_default_tuning(int32_t max_n, bbs_var_tuning *tuning);
 
 /* Plan the persistent solve of `batch` (FP64, BiCGSTAB or CG, Jacobi or

@@ -132,7 +132,7 @@ bbs_status check_tuning(const bbs_var_tuning* t) {
         if (t->stage_values[b] != 0 && t->stage_values[b] != 1)
             return errf(BBS_ERR_INVALID_ARG, "stage_values must be 0 or 1");
         if (t->pack[b] != 0 && t->pack[b] != 1) return errf(BBS_ERR_INVALID_ARG, "pack must be 0 or 1");
-        if (t->wide[b] != 0 && t->wide[b] != 1) return errf(BBS_ERR_INVALID_ARG, "wide must be 0 or 1");
+        if (t->wide[b] < 0 || t->wide[b] > 3) return errf(BBS_ERR_INVALID_ARG, "wide must be 0..3");
     }
     return BBS_OK;
 }
@@ -280,7 +280,9 @@ bbs_status build_plan(bbs_handle* h, const PlanInputs& in, bbs_var_plan** out) {
         if (packed[i]) continue;
         const int p = in.host->sys_pattern[sys[i]];
         const int n = in.host->pat_n[p];
-        if (wide_ok && t.wide[bucket[i]]) {
+        // wide bit 1: rows of at most 4 stored values on average; bit 2: denser
+        const int density_bit = in.host->pat_nnz[p] <= 4 * n ? 1 : 2;
+        if (wide_ok && (t.wide[bucket[i]] & density_bit)) {
             const int w = pow2_at_least((n + 32 * bbs::kVarWideMaxR - 1) / (32 * bbs::kVarWideMaxR));
             const int R = (n + 32 * w - 1) / (32 * w);
             const size_t smem = bbs::varwide_smem(n, in.host->pat_nnz[p]);
@@ -608,7 +610,9 @@ void default_tuning(int32_t max_n, bbs_var_tuning* t) {
         t->team_warps[b] = pow2_at_least((e + 32 * 5 - 1) / (32 * 5));
         t->stage_values[b] = 0;
         t->pack[b] = 1;
-        t->wide[b] = e > 512 ? 1 : 0;  // measured: wide teams pay above 512 rows
+        // measured on GB300: wide teams pay above 512 rows for 3-point rows
+        // (18 % faster), not for 5- and 9-point rows, nor at 512 rows or less
+        t->wide[b] = e > 512 ? 1 : 0;
         ++b;
         if (e >= max_n) break;
     }
@@ -866,10 +870,12 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
             }
             int bestwide = 0;
             if (o->solver == BBS_SOLVER_BICGSTAB && o->precond == BBS_PREC_JACOBI && nk > 32 * 8) {
-                const double per = trial(k, bw, bestw, bests, bestp, 1);
-                if (prefer(per, best, base.wide[k] != 0)) {
-                    best = per;
-                    bestwide = 1;
+                for (int bit : {1, 2}) {  // sparse rows, then denser rows
+                    const double per = trial(k, bw, bestw, bests, bestp, bestwide | bit);
+                    if (prefer(per, best, (base.wide[k] & bit) != 0)) {
+                        best = per;
+                        bestwide |= bit;
+                    }
                 }
             }
             if (!std::isfinite(best)) {

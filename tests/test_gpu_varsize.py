@@ -73,7 +73,7 @@ def test_tuned_plans_match_oracle(bbs, handle, uneven):
     tuning = bbs.bbs_var_tune(handle, vbd, b, x0, opts, sample=128)
     d = tuning.as_dict()
     assert d["block_warps"] in (8, 16) and all(w in (1, 2, 4, 8, 16) for w in d["team_warps"])
-    assert all(p in (0, 1) for p in d["pack"]) and all(w in (0, 1) for w in d["wide"])
+    assert all(p in (0, 1) for p in d["pack"]) and all(w in (0, 1, 2, 3) for w in d["wide"])
     assert np.array_equal(x0.cpu().numpy(), uneven.x0)  # the tuner leaves x0 alone
     plan = bbs.VarPlan(handle, vbd, opts, tuning)
     got = run_plan(bbs, plan, uneven)
@@ -206,7 +206,7 @@ def test_wide_teams(bbs, handle, uneven):
     t1 = bbs.bbs_var_default_tuning(1024)
     assert t1.as_dict()["wide"] == [int(e > 512) for e in t1.as_dict()["bucket_max_n"]]
     for k in range(t1.num_buckets):
-        t1.wide[k] = 1
+        t1.wide[k] = 3  # sparse and denser rows
     plan = bbs.VarPlan(handle, vbd, opts, t1)
     d = plan.describe()
     n, nnz = uneven.sys_n(), uneven.sys_nnz()
@@ -227,6 +227,11 @@ def test_wide_teams(bbs, handle, uneven):
     assert d0["wide_systems"] == 0 and d0["team_systems"] == d["team_systems"] + len(large)
     got0 = run_plan(bbs, plan0, uneven)
     assert np.array_equal(got0[3], got[3])
+    # the sparse-rows bit alone takes only the systems of at most 4 values a row
+    for k in range(t1.num_buckets):
+        t1.wide[k] = 1
+    sparse = (nnz <= 4 * n)
+    assert bbs.VarPlan(handle, vbd, opts, t1).describe()["wide_systems"] == int(((n > 256) & fits & sparse).sum())
     # BiCGSTAB without Jacobi and CG keep every team in the persistent launch
     for kw in (dict(precond="none"), dict(solver="cg")):
         assert bbs.VarPlan(handle, vbd, bbs.bbs_default_options(**kw)).describe()["wide_systems"] == 0
