@@ -384,7 +384,9 @@ bbs_status bbs_var_plan_destroy(bbs_var_plan *plan);
  * size and staging choice (and both block shapes), then packing and wide
  * teams where the bucket has such systems, and write the fastest choices to
  * *tuning (packing and wide teams keep the default tuning's choice unless the
- * other one times at least 3 % faster). b and x0 are DEVICE arrays of the batch; x0 is not
+ * other one times at least 3 % faster; then the sample of the whole batch
+ * decides whether to pack the small systems that buckets timed alone left
+ * unpacked, and whether to keep the wide teams, each by a 1 % margin). b and x0 are DEVICE arrays of the batch; x0 is not
  * modified (trials run on a private copy). Synchronous; allocates and frees
  * its own scratch. */
 bbs_status bbs_var_tune(bbs_handle *handle, const bbs_var_batch *batch,

@@ -793,23 +793,19 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
     cudaEventCreate(&e1);
     bbs_log lg{dit, drr, dst, nullptr};
 
-    // per-system time of one launch choice on bucket k's sample (INFINITY if
-    // the choice cannot be planned)
-    auto trial = [&](int k, int bw, int w, int stg, int pack, int wide) -> double {
-        PlanInputs in{vb, host, o, {}, samp[k].data(), (int)samp[k].size()};
-        std::memset(&in.t, 0, sizeof in.t);
-        in.t.num_buckets = 1;
-        in.t.bucket_max_n[0] = 2048;
-        in.t.team_warps[0] = w;
-        in.t.stage_values[0] = stg;
-        in.t.pack[0] = pack;
-        in.t.wide[0] = wide;
-        in.t.block_warps = bw;
+    // per-system time of a plan of the systems `sys` (INFINITY if the
+    // choice cannot be planned)
+    auto time_plan = [&](const bbs_var_tuning& t, const std::vector<int>& sys) -> double {
+        PlanInputs in{vb, host, o, t, sys.data(), (int)sys.size()};
         bbs_var_plan* pl = nullptr;
         if (build_plan(h, in, &pl) != BBS_OK) return INFINITY;
         float ms_sum = 0.f;
         bool ok = true;
-        for (int rep = 0; rep < 4 && ok; ++rep) {
+        // one untimed run, then at least three timed ones and until 10 ms
+        // are timed (a small bucket's trial takes a fraction of a
+        // millisecond, where one run's noise exceeds the margins below)
+        int timed = 0;
+        for (int rep = 0; ok && (rep < 4 || (ms_sum < 10.f && rep < 64)); ++rep) {
             cudaMemcpyAsync(dx, x0, sizeof(double) * vec_len, cudaMemcpyDeviceToDevice, st);
             cudaEventRecord(e0, st);
             ok = bbs_var_solve(pl, b, dx, &lg, st) == BBS_OK;
@@ -817,11 +813,34 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) ms_sum += ms;
+            if (rep > 0) {
+                ms_sum += ms;
+                ++timed;
+            }
         }
         bbs_var_plan_destroy(pl);
-        return ok ? ms_sum / 3.0 / samp[k].size() : INFINITY;
+        return ok ? ms_sum / timed / sys.size() : INFINITY;
     };
+    // one launch choice on bucket k's sample alone
+    auto trial = [&](int k, int bw, int w, int stg, int pack, int wide) -> double {
+        bbs_var_tuning t;
+        std::memset(&t, 0, sizeof t);
+        t.num_buckets = 1;
+        t.bucket_max_n[0] = 2048;
+        t.team_warps[0] = w;
+        t.stage_values[0] = stg;
+        t.pack[0] = pack;
+        t.wide[0] = wide;
+        t.block_warps = bw;
+        return time_plan(t, samp[k]);
+    };
+    std::vector<int> all_samples;
+    std::vector<char> has_small(B, 0);
+    for (int k = 0; k < B; ++k) {
+        all_samples.insert(all_samples.end(), samp[k].begin(), samp[k].end());
+        for (int i : samp[k])
+            if (host->pat_n[host->sys_pattern[i]] <= kVarPackMaxN) has_small[k] = 1;
+    }
 
     bbs_var_tuning best_overall = base;
     double best_total = INFINITY;
@@ -887,6 +906,42 @@ bbs_status bbs_var_tune(bbs_handle* h, const bbs_var_batch* vb, const bbs_var_ho
             cand.pack[k] = bestp;
             cand.wide[k] = bestwide;
             total += best * members[k].size();
+        }
+        // Packed classes and wide teams run beside the persistent launch in a
+        // full plan, which a bucket timed alone does not show. The sample of
+        // the whole batch (the real plan's shape, so a 1 % margin) decides
+        // two things: where the buckets' trials left small systems unpacked
+        // against the default, whether to pack them after all; and where wide
+        // teams are on, whether to keep them.
+        if (feasible) {
+            double t_cand = -1.0;
+            bbs_var_tuning packed = cand;
+            bool differs = false;
+            for (int k = 0; k < B; ++k)
+                if (has_small[k] && base.pack[k] && !cand.pack[k]) {
+                    packed.pack[k] = 1;
+                    differs = true;
+                }
+            if (differs) {
+                t_cand = time_plan(cand, all_samples);
+                const double t_packed = time_plan(packed, all_samples);
+                if (std::isfinite(t_packed) && t_packed <= t_cand * 1.01) {
+                    cand = packed;
+                    t_cand = t_packed;
+                }
+            }
+            bbs_var_tuning narrow = cand;
+            differs = false;
+            for (int k = 0; k < B; ++k)
+                if (cand.wide[k]) {
+                    narrow.wide[k] = 0;
+                    differs = true;
+                }
+            if (differs) {
+                if (t_cand < 0.0) t_cand = time_plan(cand, all_samples);
+                const double t_narrow = time_plan(narrow, all_samples);
+                if (std::isfinite(t_narrow) && t_narrow < t_cand * 0.99) cand = narrow;
+            }
         }
         if (feasible && total < best_total) {
             best_total = total;
